@@ -1,0 +1,91 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and the bench.
+
+This module only draws random numbers and arranges them into the inputs of the
+method (two-qubit gates, random MPS tensors, one-site operators).  It holds no
+step of pTEBD itself: no contraction, SVD, truncation or regauging.
+
+Conventions (used everywhere in this repository):
+
+* sites s = 0..N-1, bond b = 0..N-2 joins sites b and b+1;
+* a gate on bond b is a 4x4 complex matrix U[(2*s0' + s1'), (2*s0 + s1)] where
+  s0 is the physical index of site b (the most significant one) and s1 that of
+  site b+1; a layer of parity p gates every bond b with b % 2 == p;
+* the circuits are brickwork circuits of Haar-random U(4) gates: layer l has
+  parity l % 2, so the first layer gates the pairs (0,1), (2,3), ... which the
+  paper calls the odd physical layer (App. A, RQC-1D).
+
+Random streams are keyed by (seed, circuit, layer) through numpy's SeedSequence,
+so that any layer of any circuit can be regenerated on its own.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "haar_u4",
+    "layer_bonds",
+    "brickwork_layer",
+    "brickwork_circuit",
+    "random_mps_tensors",
+    "random_one_site_op",
+    "gates_to_interleaved",
+]
+
+
+def _rng(*key: int) -> np.random.Generator:
+    return np.random.default_rng([int(k) & 0xFFFFFFFF for k in key])
+
+
+def haar_u4(rng: np.random.Generator) -> np.ndarray:
+    """One Haar-random 4x4 unitary: QR of a complex Ginibre matrix with the
+    phases of R's diagonal moved into Q (Mezzadri, Notices AMS 54, 592 (2007))."""
+    z = (rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+def layer_bonds(n_sites: int, parity: int) -> np.ndarray:
+    """Bonds gated by a brickwork layer of the given parity."""
+    return np.arange(parity, n_sites - 1, 2, dtype=np.int32)
+
+
+def brickwork_layer(seed: int, n_sites: int, layer: int, circuit: int = 0):
+    """(parity, bonds, gates[n_bonds,4,4]) of one brickwork layer."""
+    parity = layer % 2
+    bonds = layer_bonds(n_sites, parity)
+    rng = _rng(seed, circuit, layer, 0x6A7E)
+    gates = np.stack([haar_u4(rng) for _ in range(len(bonds))]) if len(bonds) else np.zeros((0, 4, 4), complex)
+    return parity, bonds, gates
+
+
+def brickwork_circuit(seed: int, n_sites: int, depth: int, circuit: int = 0):
+    """List of `depth` brickwork layers, see `brickwork_layer`."""
+    return [brickwork_layer(seed, n_sites, l, circuit) for l in range(depth)]
+
+
+def random_mps_tensors(seed: int, n_sites: int, chi: int, d: int = 2):
+    """Random open-MPS tensors M[s] of shape (d, chi_left, chi_right) with
+    entries a + ib, a and b uniform in [-1, 1] (the recipe of Sec. III D used
+    for the PtSU experiment).  Bond dimensions are min(chi, d^b, d^(N-b))."""
+    rng = _rng(seed, 0x3A5, n_sites, chi)
+    dims = [1] + [min(chi, d ** (b + 1), d ** (n_sites - b - 1)) for b in range(n_sites - 1)] + [1]
+    out = []
+    for s in range(n_sites):
+        shape = (d, dims[s], dims[s + 1])
+        out.append(rng.uniform(-1.0, 1.0, shape) + 1j * rng.uniform(-1.0, 1.0, shape))
+    return out
+
+
+def random_one_site_op(seed: int, hermitian: bool = True) -> np.ndarray:
+    """A random 2x2 complex operator (Hermitian by default)."""
+    rng = _rng(seed, 0x0B5)
+    a = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+    return (a + a.conj().T) / 2 if hermitian else a
+
+
+def gates_to_interleaved(gates: np.ndarray) -> np.ndarray:
+    """(n,4,4) complex128 -> contiguous float64 array of n*32 values, each gate
+    row-major with (re, im) interleaved: the layout the C ABI takes."""
+    g = np.ascontiguousarray(np.asarray(gates, dtype=np.complex128))
+    return np.ascontiguousarray(g.view(np.float64).reshape(-1))

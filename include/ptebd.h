@@ -1,0 +1,201 @@
+/*
+ * ptebd.h - C ABI of libptebd, a single-GPU (sm_103a) implementation of one
+ * layer of the improved parallel TEBD (pTEBD) of arXiv:2312.02667.
+ *
+ * Method (all references are to the paper):
+ *   - state: an open MPS in Vidal form {Gamma^[i], Lambda^[i]} (Sec. II B);
+ *   - one gate layer (Algorithm 1, loop body): on every gated bond at once,
+ *     theta = Lambda_{i-1} Gamma_i Lambda_i Gamma_{i+1} Lambda_{i+1}, theta' = U theta,
+ *     SVD theta' = U S V^dagger, Gamma_i <- Lambda_{i-1}^{-1} U, Lambda_i <- S,
+ *     Gamma_{i+1} <- V^dagger Lambda_{i+1}^{-1} (Sec. II C);
+ *   - the parallel compression keeps the chi' largest singular values of every
+ *     bond (projector P_i, Sec. III B) and multiplies Lambda_i by
+ *     nu_i = (1 - eps_i)^{-1/2} (Sec. III C, norm stabilisation);
+ *   - g parallel trivial-simple-update steps (PtSU) follow: tSU on the paper's
+ *     odd bonds, then on its even bonds (Sec. III D, IPMC of Sec. III E).
+ *
+ * Index conventions: sites s = 0..N-1; bond b = 0..N-2 joins sites b and b+1
+ * (the paper's bond i is b = i-1).  Lambda_{-1} = Lambda_{N-1} = (1).  The
+ * physical dimension is d = 2.  A two-site gate is a 4x4 complex matrix
+ * U[(2 s0' + s1'), (2 s0 + s1)] with s0 the physical index of site b; gates
+ * are passed as 32 doubles each: row-major, (re, im) interleaved.
+ *
+ * Memory ownership: the library never allocates device memory.  The caller
+ * asks ptebd_required_bytes() for the sizes, allocates one state buffer and
+ * one workspace buffer on the current device (256-byte aligned, e.g. through
+ * the PyTorch caching allocator) and passes them to ptebd_create(); both must
+ * stay valid until ptebd_destroy().  The handle itself lives in host memory
+ * allocated by ptebd_create and freed by ptebd_destroy.
+ *
+ * Streams: every call runs on the stream given at create time (or set later
+ * with ptebd_set_stream); calls that return results to the host synchronise
+ * that stream, all others are asynchronous.
+ *
+ * Errors: every function returns an int status, 0 on success and a negative
+ * PTEBD_ERR_* code otherwise; no C++ exception crosses the ABI.
+ * ptebd_last_error() gives a text for the last failure of a handle.
+ * Errors found on the device (non-finite values, a zero two-site tensor, a
+ * discarded weight >= 1 in absolute mode, a Jacobi sweep limit, a bounded wait
+ * that ran out) are latched in a device word and reported by the next
+ * synchronising call (ptebd_sync, ptebd_norm, ptebd_get_*, ...).
+ */
+#ifndef PTEBD_H
+#define PTEBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTEBD_OK                 0
+#define PTEBD_ERR_INVALID       -1  /* bad argument (null pointer, range, parity) */
+#define PTEBD_ERR_UNSUPPORTED   -2  /* d != 2, chi_max above the compiled limit */
+#define PTEBD_ERR_MEMORY        -3  /* buffer too small or misaligned */
+#define PTEBD_ERR_CUDA          -4  /* a CUDA runtime call failed */
+#define PTEBD_ERR_OVERLAP       -5  /* two gated bonds share a site */
+#define PTEBD_ERR_NUMERIC       -6  /* device-detected non-finite value / zero tensor / eps >= 1 */
+#define PTEBD_ERR_NOT_CONVERGED -7  /* a Jacobi SVD reached its sweep limit */
+#define PTEBD_ERR_SHAPE         -8  /* imported tensor dimensions do not match the bonds */
+#define PTEBD_ERR_TIMEOUT       -9  /* a bounded device wait ran out */
+
+/* Largest chi_max of this build: theta is at most 512 x 512. */
+#define PTEBD_CHI_LIMIT 256
+
+enum ptebd_precision {
+    PTEBD_FP64 = 0,   /* complex128 Gamma and theta, FP64 everywhere */
+    PTEBD_MIXED = 1   /* complex64 Gamma, theta and SVD rotations; FP64 Lambda,
+                         nu, discarded weights, column norms and reductions */
+};
+
+enum ptebd_eps_mode {
+    PTEBD_EPS_RELATIVE = 0, /* eps_b = dropped S^2 / all S^2 (default) */
+    PTEBD_EPS_ABSOLUTE = 1  /* eps_b = dropped S^2, taken literally */
+};
+
+typedef struct ptebd_config {
+    int32_t n_sites;    /* N >= 2 */
+    int32_t d;          /* local dimension, must be 2 */
+    int32_t chi_max;    /* chi of Algorithm 1, 1..PTEBD_CHI_LIMIT */
+    int32_t precision;  /* enum ptebd_precision */
+    int32_t g;          /* PtSU steps run after every layer (0 = none) */
+    int32_t eps_mode;   /* enum ptebd_eps_mode */
+    double cutoff;      /* drop singular values <= cutoff * lambda_1 (>= 0) */
+    double floor;       /* PTEBD_MIXED only: singular values <= floor * lambda_1
+                           are below what complex64 arithmetic resolves and are
+                           dropped as well; a negative value selects 1e-6.
+                           Ignored (treated as 0) for PTEBD_FP64. */
+} ptebd_config;
+
+typedef struct ptebd_state ptebd_state;
+
+/* Sizes of the two device buffers ptebd_create needs for this config.
+ * workspace_bytes is the size that processes a whole layer in one pass;
+ * any workspace of at least workspace_min_bytes works (layers are then split
+ * into chunks of bonds).  Any output pointer may be NULL. */
+int ptebd_required_bytes(const ptebd_config* cfg, size_t* state_bytes,
+                         size_t* workspace_bytes, size_t* workspace_min_bytes);
+
+/* Create a state in |0...0> (all bond dimensions 1, Sec. IV A) inside the
+ * caller's device buffers.  stream is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns nothing on the device; destroy frees the host
+ * handle only. */
+int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes,
+                 void* workspace, size_t workspace_bytes, void* stream,
+                 ptebd_state** out);
+int ptebd_destroy(ptebd_state* st);
+int ptebd_set_stream(ptebd_state* st, void* stream);
+int ptebd_reset(ptebd_state* st);                 /* back to |0...0>, counters cleared */
+const char* ptebd_last_error(const ptebd_state* st);
+int ptebd_get_config(const ptebd_state* st, ptebd_config* out);
+
+/* One brickwork layer (Algorithm 1, loop body; Sec. II C and III B-E):
+ * gates[j] acts on bond b = parity + 2 j for j < n_p = ceil((N - 1 - parity) / 2).
+ * gates: n_p * 32 doubles (see the layout above), in host memory when
+ * gates_on_device == 0, else in device memory on this GPU.  Asynchronous.
+ * Runs the TEBD procedure with compression and nu on every gated bond, then
+ * the config's g PtSU steps. */
+int ptebd_apply_layer(ptebd_state* st, const double* gates, int32_t parity,
+                      int32_t gates_on_device);
+
+/* Same on an arbitrary set of pairwise non-adjacent bonds (compiled layers of
+ * routed circuits, App. A).  bonds: n_bonds host int32 values in [0, N-2];
+ * two bonds closer than 2 return PTEBD_ERR_OVERLAP. */
+int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds,
+                      const double* gates, int32_t gates_on_device);
+
+/* g explicit PtSU steps (Sec. III D): tSU (identity gate skipped, no nu, same
+ * truncation rule) on bonds 0, 2, 4, ... then on bonds 1, 3, 5, ...  */
+int ptebd_regauge(ptebd_state* st, int32_t g);
+
+/* Wait for all work of the handle and report latched device errors. */
+int ptebd_sync(ptebd_state* st);
+
+/* Full contractions (exact for any MPS, canonical or not; synchronous).
+ * norm: n = || |Psi> ||.  overlap: <a|b> as out[0] + i out[1] (a and b must
+ * have the same N and live on the same device).  expect: <Psi|O|Psi>/<Psi|Psi>
+ * for a one-site operator O (2x2, 8 doubles, O[s', s] row-major interleaved)
+ * on `site`, and expect2 for a two-site operator (4x4 in the gate layout) on
+ * sites (site, site+1).  The transfer matrices are accumulated in FP64. */
+int ptebd_norm(ptebd_state* st, double* out);
+int ptebd_overlap(ptebd_state* a, ptebd_state* b, double out[2]);
+int ptebd_expect(ptebd_state* st, int32_t site, const double* op, double out[2]);
+int ptebd_expect2(ptebd_state* st, int32_t site, const double* op, double out[2]);
+
+/* State interchange (host buffers; synchronous).
+ * get_chi: N-1 bond dimensions.  get_lambda: Lambda_b (chi_b doubles; the
+ * buffer must hold chi_max).  get_site / set_site: Gamma_s as
+ * (2, chi_{s-1}, chi_s) complex128, C order, interleaved (re, im); set_site
+ * requires chi_l == chi_{s-1} and chi_r == chi_s (PTEBD_ERR_SHAPE otherwise).
+ * set_lambda sets chi_b = k and Lambda_b (k values, descending expected). */
+int ptebd_get_chi(ptebd_state* st, int32_t* chi_out);
+int ptebd_get_lambda(ptebd_state* st, int32_t bond, double* out, int32_t* k);
+int ptebd_get_site(ptebd_state* st, int32_t site, int32_t* chi_l, int32_t* chi_r,
+                   double* gamma_out);
+int ptebd_set_lambda(ptebd_state* st, int32_t bond, int32_t k, const double* values);
+int ptebd_set_site(ptebd_state* st, int32_t site, int32_t chi_l, int32_t chi_r,
+                   const double* gamma);
+
+/* Metrics (synchronous).  eps_total = sum over all gated bonds of all layers
+ * so far of eps_b (Theorem 1's epsilon); log_nu_total = sum of ln nu_b, so
+ * prod nu_i = exp(log_nu_total) (Sec. III C, n* = n prod nu_i).  Per-bond
+ * values of the most recent gate update of each bond: eps_b, nu_b and the
+ * number of singular values of its theta' (rank_in = min(rows, cols)); a bond
+ * never gated holds eps 0, nu 1, rank_in 0.  Any output pointer may be NULL. */
+int ptebd_trunc_error(ptebd_state* st, double* eps_total, double* log_nu_total);
+int ptebd_bond_stats(ptebd_state* st, double* eps, double* nu, int32_t* rank_in);
+/* Jacobi sweeps of the most recent SVD of every bond (tSU or gate) and the
+ * number of layers applied so far. */
+int ptebd_svd_sweeps(ptebd_state* st, int32_t* sweeps, int32_t* layers);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch of the layer kernels.  ptebd_timing(st, 1) clears the counters
+ * and starts recording, ptebd_timing(st, 0) stops.  ptebd_timing_read
+ * (synchronous) returns, for each kernel kind (PTEBD_K_*), the summed device
+ * time in milliseconds and the number of launches; n_kinds entries are
+ * written (at most PTEBD_K_COUNT). */
+#define PTEBD_K_THETA 0     /* theta' = U theta (Sec. II C) */
+#define PTEBD_K_SVD 1       /* one-sided Jacobi SVD */
+#define PTEBD_K_TRUNCATE 2  /* sort, projector P_b, eps_b, nu_b, Lambda_b */
+#define PTEBD_K_GAMMA 3     /* Gamma_b and Gamma_{b+1} rebuild */
+#define PTEBD_K_REDUCE 4    /* per-layer eps / ln nu sums */
+#define PTEBD_K_COUNT 5
+int ptebd_timing(ptebd_state* st, int32_t enable);
+int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_kinds);
+
+/* Work counters accumulated on the device since create / reset (synchronous):
+ * out[0] = sum over every SVD of (sweeps x cols (cols - 1) / 2 x rows), the
+ *          column-pair-row visits of the one-sided Jacobi (its nominal cost is
+ *          28 real flops per visit: an 8-flop complex dot and a 20-flop
+ *          complex rotation of two entries);
+ * out[1] = sum over every theta' of 32 chi_{b-1} chi_b chi_{b+1} (the real
+ *          flops of the four complex products X_s Y_t);
+ * out[2] = Jacobi rotations actually applied.  n entries are written (<= 3). */
+int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTEBD_H */

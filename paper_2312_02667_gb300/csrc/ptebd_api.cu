@@ -1,0 +1,816 @@
+// C ABI of libptebd (declared in include/ptebd.h): state layout in the caller's
+// device buffers, the layer driver of Algorithm 1 (arXiv:2312.02667) and the
+// host side of the contractions.  All device work is issued on the handle's
+// stream; the library never allocates device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ptebd_internal.h"
+
+using namespace ptebd;
+
+struct ptebd_state {
+    ptebd_config cfg;
+    Layout L;
+    char* mem = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int slots = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int layers = 0;
+    std::string last_error;
+    // per-kernel CUDA-event timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;  // kind of each recorded (start, stop) pair
+    ~ptebd_state() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+namespace ptebd {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int chip_for(int chi_max) {
+    int c = 16;
+    while (c < chi_max) c <<= 1;
+    return c;
+}
+
+Layout make_layout(const ptebd_config& cfg) {
+    Layout L;
+    L.n_sites = cfg.n_sites;
+    L.chi_max = cfg.chi_max;
+    L.chip = chip_for(cfg.chi_max);
+    L.ldw = 2 * L.chip;
+    L.precision = cfg.precision;
+    L.max_bonds = cfg.n_sites / 2;  // ceil((N-1)/2)
+    L.elem = cfg.precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
+    const size_t N = (size_t)cfg.n_sites, chip = (size_t)L.chip, nb = (size_t)L.max_bonds;
+    size_t o = 0;
+    L.off_gamma = o; o = align256(o + N * 2 * chip * chip * L.elem);
+    L.off_lam = o; o = align256(o + (N + 1) * chip * sizeof(double));
+    L.off_chi = o; o = align256(o + (N + 1) * sizeof(int32_t));
+    L.off_bond_eps = o; o = align256(o + N * sizeof(double));
+    L.off_bond_nu = o; o = align256(o + N * sizeof(double));
+    L.off_bond_rank = o; o = align256(o + N * sizeof(int32_t));
+    L.off_bond_sweeps = o; o = align256(o + N * sizeof(int32_t));
+    L.off_totals = o; o = align256(o + 8 * sizeof(double) + 4 * sizeof(unsigned long long));
+    L.off_err = o; o = align256(o + sizeof(uint32_t));
+    L.off_gates = o; o = align256(o + nb * 32 * sizeof(double));
+    L.off_bonds = o; o = align256(o + 3 * nb * sizeof(int32_t));
+    L.off_scratch = o; o = align256(o + 8 * chip * chip * sizeof(double2) + 8 * sizeof(double));
+    L.state_bytes = o;
+    const size_t ldw = (size_t)L.ldw;
+    L.slot_w = align256(ldw * ldw * L.elem);
+    L.slot_small = 2 * ldw * sizeof(double) + ldw * sizeof(int32_t) + 8 * sizeof(int32_t) + 2 * sizeof(double) +
+                   sizeof(int32_t);
+    L.slot_bytes = 2 * L.slot_w + L.slot_small;
+    return L;
+}
+
+}  // namespace ptebd
+
+namespace {
+
+// Workspace regions for `slots` slots.
+struct WsView {
+    void* w; void* w0; double* norms; double* sig; int32_t* perm; int32_t* dims;
+    double* slot_eps; double* slot_lognu; int32_t* slot_sweeps; size_t bytes;
+};
+
+WsView ws_view(const Layout& L, char* base, int slots) {
+    WsView v{};
+    const size_t ldw = (size_t)L.ldw, s = (size_t)slots;
+    size_t o = 0;
+    v.w = base + o; o = align256(o + s * L.slot_w);
+    v.w0 = base + o; o = align256(o + s * L.slot_w);
+    v.norms = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
+    v.sig = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
+    v.perm = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * ldw * sizeof(int32_t));
+    v.dims = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * 8 * sizeof(int32_t));
+    v.slot_eps = reinterpret_cast<double*>(base + o); o = align256(o + s * sizeof(double));
+    v.slot_lognu = reinterpret_cast<double*>(base + o); o = align256(o + s * sizeof(double));
+    v.slot_sweeps = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * sizeof(int32_t));
+    v.bytes = o;
+    return v;
+}
+
+size_t ws_bytes_for(const Layout& L, int slots) { return ws_view(L, nullptr, slots).bytes; }
+
+int set_err(ptebd_state* st, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int set_err(ptebd_state* st, int code, const char* fmt, ...) {
+    if (st) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        st->last_error = buf;
+    }
+    return code;
+}
+
+#define CUDA_TRY(st, call)                                                                              \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return set_err((st), PTEBD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+    } while (0)
+
+int validate_config(const ptebd_config* c, std::string* why) {
+    if (!c) { *why = "null config"; return PTEBD_ERR_INVALID; }
+    if (c->d != 2) { *why = "only d = 2 is supported"; return PTEBD_ERR_UNSUPPORTED; }
+    if (c->n_sites < 2) { *why = "n_sites must be >= 2"; return PTEBD_ERR_INVALID; }
+    if (c->chi_max < 1) { *why = "chi_max must be >= 1"; return PTEBD_ERR_INVALID; }
+    if (c->chi_max > PTEBD_CHI_LIMIT) { *why = "chi_max above PTEBD_CHI_LIMIT"; return PTEBD_ERR_UNSUPPORTED; }
+    if (c->precision != PTEBD_FP64 && c->precision != PTEBD_MIXED) { *why = "bad precision"; return PTEBD_ERR_INVALID; }
+    if (c->eps_mode != PTEBD_EPS_RELATIVE && c->eps_mode != PTEBD_EPS_ABSOLUTE) { *why = "bad eps_mode"; return PTEBD_ERR_INVALID; }
+    if (c->g < 0) { *why = "g must be >= 0"; return PTEBD_ERR_INVALID; }
+    if (!(c->cutoff >= 0.0) || !std::isfinite(c->cutoff)) { *why = "cutoff must be finite and >= 0"; return PTEBD_ERR_INVALID; }
+    if (std::isnan(c->floor)) { *why = "floor is NaN"; return PTEBD_ERR_INVALID; }
+    return PTEBD_OK;
+}
+
+double effective_threshold(const ptebd_config& c) {
+    double fl = 0.0;
+    if (c.precision == PTEBD_MIXED) fl = c.floor < 0.0 ? 1e-6 : c.floor;
+    return std::max(c.cutoff, fl);
+}
+
+template <typename T> T* at(char* base, size_t off) { return reinterpret_cast<T*>(base + off); }
+
+__global__ void k_init_state(char* mem, Layout L) {
+    const size_t N = (size_t)L.n_sites, chip = (size_t)L.chip, slice = chip * chip;
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    double* lam = reinterpret_cast<double*>(mem + L.off_lam);
+    int32_t* chi = reinterpret_cast<int32_t*>(mem + L.off_chi);
+    double* nu = reinterpret_cast<double*>(mem + L.off_bond_nu);
+    int32_t* bonds = reinterpret_cast<int32_t*>(mem + L.off_bonds);
+    for (size_t s = tid; s < N; s += stride) {
+        // |0>: Gamma_s[0](0,0) = 1
+        if (L.precision == PTEBD_FP64)
+            reinterpret_cast<double2*>(mem + L.off_gamma)[s * 2 * slice] = make_double2(1.0, 0.0);
+        else
+            reinterpret_cast<float2*>(mem + L.off_gamma)[s * 2 * slice] = make_float2(1.f, 0.f);
+        nu[s] = 1.0;
+    }
+    for (size_t r = tid; r <= N; r += stride) { lam[r * chip] = 1.0; chi[r] = 1; }
+    const size_t nb = (size_t)L.max_bonds;
+    for (size_t i = tid; i < nb; i += stride) {
+        bonds[i] = (int32_t)(2 * i);                                   // even bonds
+        bonds[nb + i] = (2 * i + 1 <= N - 2) ? (int32_t)(2 * i + 1) : -1;  // odd bonds
+    }
+}
+
+int n_parity_bonds(int n_sites, int parity) { return parity == 0 ? n_sites / 2 : (n_sites - 1) / 2; }
+
+cudaEvent_t next_event(ptebd_state* st) {
+    if (st->ev_used == st->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        st->ev_pool.push_back(e);
+    }
+    return st->ev_pool[st->ev_used++];
+}
+
+// Launch `f` and, when timing is on, bracket it with events of kind `kind`.
+template <typename F>
+cudaError_t timed(ptebd_state* st, int kind, F&& f) {
+    if (!st->timing) return f();
+    cudaEvent_t a = next_event(st), b = next_event(st);
+    if (!a || !b) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(a, st->stream);
+    if (e != cudaSuccess) return e;
+    e = f();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b, st->stream);
+    st->ev_kind.push_back(kind);
+    return e;
+}
+
+template <typename R>
+int run_bonds(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_gates, bool gated) {
+    const Layout& L = st->L;
+    char* m = st->mem;
+    WsView ws = ws_view(L, st->ws, st->slots);
+    LayerArgs<R> a{};
+    a.gamma = at<cx_t<R>>(m, L.off_gamma);
+    a.lam = at<double>(m, L.off_lam);
+    a.chi = at<int32_t>(m, L.off_chi);
+    a.w = reinterpret_cast<cx_t<R>*>(ws.w);
+    a.w0 = reinterpret_cast<cx_t<R>*>(ws.w0);
+    a.norms = ws.norms; a.sig = ws.sig; a.perm = ws.perm; a.dims = ws.dims;
+    a.slot_eps = ws.slot_eps; a.slot_lognu = ws.slot_lognu; a.slot_sweeps = ws.slot_sweeps;
+    a.chip = L.chip; a.ldw = L.ldw; a.n_sites = L.n_sites; a.chi_max = L.chi_max;
+    a.thr_rel = effective_threshold(st->cfg);
+    a.eps_mode = st->cfg.eps_mode;
+    a.stabilise = gated ? 1 : 0;
+    a.max_sweeps = 40;
+    a.bond_eps = at<double>(m, L.off_bond_eps);
+    a.bond_nu = at<double>(m, L.off_bond_nu);
+    a.bond_rank = at<int32_t>(m, L.off_bond_rank);
+    a.bond_sweeps = at<int32_t>(m, L.off_bond_sweeps);
+    a.totals = at<double>(m, L.off_totals);
+    a.err = at<uint32_t>(m, L.off_err);
+    a.work = reinterpret_cast<unsigned long long*>(at<double>(m, L.off_totals) + 8);
+    cudaStream_t s = st->stream;
+    for (int c0 = 0; c0 < nb; c0 += st->slots) {
+        a.count = std::min(st->slots, nb - c0);
+        a.bonds = d_bonds + c0;
+        a.gates = gated ? d_gates + (size_t)c0 * 32 : nullptr;
+        CUDA_TRY(st, timed(st, PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
+        CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
+        CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
+        CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
+        CUDA_TRY(st, timed(st, PTEBD_K_REDUCE, [&] {
+                     return launch_reduce_layer(a.slot_eps, a.slot_lognu, a.count, gated ? 1 : 0, a.totals, s);
+                 }));
+    }
+    return PTEBD_OK;
+}
+
+int run(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_gates, bool gated) {
+    if (nb <= 0) return PTEBD_OK;
+    return st->cfg.precision == PTEBD_FP64 ? run_bonds<double>(st, d_bonds, nb, d_gates, gated)
+                                           : run_bonds<float>(st, d_bonds, nb, d_gates, gated);
+}
+
+int regauge_steps(ptebd_state* st, int g) {
+    const Layout& L = st->L;
+    const int32_t* lists = at<int32_t>(st->mem, L.off_bonds);
+    for (int step = 0; step < g; ++step) {
+        int r = run(st, lists, n_parity_bonds(L.n_sites, 0), nullptr, false);
+        if (r) return r;
+        r = run(st, lists + L.max_bonds, n_parity_bonds(L.n_sites, 1), nullptr, false);
+        if (r) return r;
+    }
+    return PTEBD_OK;
+}
+
+const double* stage_gates(ptebd_state* st, const double* gates, int n, int on_device, int* rc) {
+    *rc = PTEBD_OK;
+    if (on_device) return gates;
+    double* dst = at<double>(st->mem, st->L.off_gates);
+    cudaError_t e = cudaMemcpyAsync(dst, gates, (size_t)n * 32 * sizeof(double), cudaMemcpyHostToDevice, st->stream);
+    if (e != cudaSuccess) *rc = set_err(st, PTEBD_ERR_CUDA, "gate upload failed: %s", cudaGetErrorString(e));
+    return dst;
+}
+
+int check_device_errors(ptebd_state* st) {
+    uint32_t err = 0;
+    uint32_t* d_err = at<uint32_t>(st->mem, st->L.off_err);
+    CUDA_TRY(st, cudaMemcpyAsync(&err, d_err, sizeof err, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (!err) return PTEBD_OK;
+    CUDA_TRY(st, cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (err & DERR_TIMEOUT) return set_err(st, PTEBD_ERR_TIMEOUT, "a bounded device wait ran out (0x%x)", err);
+    if (err & DERR_NONFINITE) return set_err(st, PTEBD_ERR_NUMERIC, "non-finite singular value (0x%x)", err);
+    if (err & DERR_ZERO_THETA) return set_err(st, PTEBD_ERR_NUMERIC, "zero two-site tensor (0x%x)", err);
+    if (err & DERR_EPS) return set_err(st, PTEBD_ERR_NUMERIC, "discarded weight >= 1, nu undefined (0x%x)", err);
+    if (err & DERR_NOT_CONVERGED) return set_err(st, PTEBD_ERR_NOT_CONVERGED, "Jacobi sweep limit reached (0x%x)", err);
+    return set_err(st, PTEBD_ERR_NUMERIC, "device error 0x%x", err);
+}
+
+int sync_and_check(ptebd_state* st) {
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    return check_device_errors(st);
+}
+
+std::vector<int32_t> host_chi(ptebd_state* st, int* rc) {
+    std::vector<int32_t> chi((size_t)st->L.n_sites + 1);
+    *rc = PTEBD_OK;
+    cudaError_t e = cudaMemcpyAsync(chi.data(), at<int32_t>(st->mem, st->L.off_chi), chi.size() * sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+    if (e != cudaSuccess) *rc = set_err(st, PTEBD_ERR_CUDA, "reading bond dimensions failed: %s", cudaGetErrorString(e));
+    return chi;
+}
+
+// ------------------------------------------------------------ contraction --
+struct Chain {
+    ptebd_state* st;       // owns the scratch and the stream
+    double2* mat[8];
+    double* logacc;
+};
+
+Chain chain_of(ptebd_state* st) {
+    Chain c;
+    c.st = st;
+    const size_t chip = (size_t)st->L.chip;
+    double2* base = at<double2>(st->mem, st->L.off_scratch);
+    for (int i = 0; i < 8; ++i) c.mat[i] = base + (size_t)i * chip * chip;
+    c.logacc = reinterpret_cast<double*>(base + 8 * chip * chip);
+    return c;
+}
+
+template <typename TB>
+const TB* gamma_ptr(ptebd_state* st, int site, int sigma) {
+    const size_t chip = (size_t)st->L.chip;
+    return reinterpret_cast<const TB*>(st->mem + st->L.off_gamma) + ((size_t)site * 2 + sigma) * chip * chip;
+}
+const double* lam_ptr(ptebd_state* st, int bond) {  // bond in -1..N-1
+    return at<double>(st->mem, st->L.off_lam) + (size_t)(bond + 1) * st->L.chip;
+}
+
+// Generic GEMM dispatch on the precisions of the two operands.
+int gemm(ptebd_state* owner, int m, int n, int k, double2 alpha, const void* A, bool a64, int lda, int opA,
+         const void* B, bool b64, int ldb, const double* colscale, double2 beta, double2* Cm, int ldc,
+         const double* rowscale) {
+    cudaError_t e;
+    cudaStream_t s = owner->stream;
+    if (a64 && b64)
+        e = launch_zgemm<double2, double2>(m, n, k, alpha, (const double2*)A, lda, opA, (const double2*)B, ldb,
+                                           colscale, beta, Cm, ldc, rowscale, s);
+    else if (a64)
+        e = launch_zgemm<double2, float2>(m, n, k, alpha, (const double2*)A, lda, opA, (const float2*)B, ldb,
+                                          colscale, beta, Cm, ldc, rowscale, s);
+    else if (b64)
+        e = launch_zgemm<float2, double2>(m, n, k, alpha, (const float2*)A, lda, opA, (const double2*)B, ldb,
+                                          colscale, beta, Cm, ldc, rowscale, s);
+    else
+        e = launch_zgemm<float2, float2>(m, n, k, alpha, (const float2*)A, lda, opA, (const float2*)B, ldb,
+                                         colscale, beta, Cm, ldc, rowscale, s);
+    if (e != cudaSuccess) return set_err(owner, PTEBD_ERR_CUDA, "gemm launch failed: %s", cudaGetErrorString(e));
+    return PTEBD_OK;
+}
+
+const void* gptr(ptebd_state* st, int site, int sigma) {
+    return st->cfg.precision == PTEBD_FP64 ? (const void*)gamma_ptr<double2>(st, site, sigma)
+                                           : (const void*)gamma_ptr<float2>(st, site, sigma);
+}
+bool is64(ptebd_state* st) { return st->cfg.precision == PTEBD_FP64; }
+
+const double2 ONE = {1.0, 0.0};
+const double2 ZERO = {0.0, 0.0};
+
+// <a| O |b> with O = identity everywhere except a one-site op on `site1` or a
+// two-site op on (site2, site2+1) (both -1 for none).  op is row-major complex.
+int contract(ptebd_state* a, ptebd_state* b, int site1, int site2, const double* op, double out[2]) {
+    ptebd_state* own = a;
+    Chain ch = chain_of(own);
+    int rc;
+    std::vector<int32_t> ca = host_chi(a, &rc);
+    if (rc) return rc;
+    std::vector<int32_t> cb = host_chi(b, &rc);
+    if (rc) return rc;
+    const int N = a->L.n_sites, lda_a = a->L.chip, lda_b = b->L.chip, ldc = own->L.chip;
+    double2* E = ch.mat[0];
+    double2* En = ch.mat[1];
+    CUDA_TRY(own, cudaMemsetAsync(ch.logacc, 0, sizeof(double), own->stream));
+    CUDA_TRY(own, launch_fill_identity(E, 1, 1, ldc, own->stream));
+    auto opc = [&](int r, int c, int dim) { return make_double2(op[2 * (r * dim + c)], op[2 * (r * dim + c) + 1]); };
+    int s = 0;
+    while (s < N) {
+        const int al = ca[s], ar = ca[s + 1], bl = cb[s], br = cb[s + 1];
+        const double* lamA = lam_ptr(a, s);
+        const double* lamB = lam_ptr(b, s);
+        if (s == site1) {
+            // T_x = sum_y O[x,y] E M_b[y];  E' = sum_x M_a[x]^dag T_x
+            for (int x = 0; x < 2; ++x)
+                for (int y = 0; y < 2; ++y)
+                    if ((rc = gemm(own, al, br, bl, opc(x, y, 2), E, true, ldc, 0, gptr(b, s, y), is64(b), lda_b, lamB,
+                                   y == 0 ? ZERO : ONE, ch.mat[2 + x], ldc, nullptr)))
+                        return rc;
+            for (int x = 0; x < 2; ++x)
+                if ((rc = gemm(own, ar, br, al, ONE, gptr(a, s, x), is64(a), lda_a, 1, ch.mat[2 + x], true, ldc,
+                               nullptr, x == 0 ? ZERO : ONE, En, ldc, lamA)))
+                    return rc;
+            s += 1;
+        } else if (s == site2) {
+            const int bm = cb[s + 2], am = ca[s + 2];
+            const double* lamB2 = lam_ptr(b, s + 1);
+            const double* lamA2 = lam_ptr(a, s + 1);
+            // R_y = E M_b,s[y]  (al x br)
+            for (int y = 0; y < 2; ++y)
+                if ((rc = gemm(own, al, br, bl, ONE, E, true, ldc, 0, gptr(b, s, y), is64(b), lda_b, lamB, ZERO,
+                               ch.mat[2 + y], ldc, nullptr)))
+                    return rc;
+            // X_xz = sum_{y,w} O[(x z), (y w)] R_y M_b,s+1[w]   (al x bm)
+            for (int x = 0; x < 2; ++x)
+                for (int z = 0; z < 2; ++z) {
+                    double2* X = ch.mat[4 + 2 * x + z];
+                    bool first = true;
+                    for (int y = 0; y < 2; ++y)
+                        for (int w = 0; w < 2; ++w) {
+                            if ((rc = gemm(own, al, bm, br, opc(2 * x + z, 2 * y + w, 4), ch.mat[2 + y], true, ldc, 0,
+                                           gptr(b, s + 1, w), is64(b), lda_b, lamB2, first ? ZERO : ONE, X, ldc,
+                                           nullptr)))
+                                return rc;
+                            first = false;
+                        }
+                }
+            // E' = sum_{x,z} M_a,s+1[z]^dag (M_a,s[x]^dag X_xz)
+            bool firstE = true;
+            for (int x = 0; x < 2; ++x)
+                for (int z = 0; z < 2; ++z) {
+                    double2* Y = ch.mat[2];
+                    if ((rc = gemm(own, ar, bm, al, ONE, gptr(a, s, x), is64(a), lda_a, 1, ch.mat[4 + 2 * x + z], true,
+                                   ldc, nullptr, ZERO, Y, ldc, lamA)))
+                        return rc;
+                    if ((rc = gemm(own, am, bm, ar, ONE, gptr(a, s + 1, z), is64(a), lda_a, 1, Y, true, ldc, nullptr,
+                                   firstE ? ZERO : ONE, En, ldc, lamA2)))
+                        return rc;
+                    firstE = false;
+                }
+            s += 2;
+        } else {
+            for (int x = 0; x < 2; ++x) {
+                if ((rc = gemm(own, al, br, bl, ONE, E, true, ldc, 0, gptr(b, s, x), is64(b), lda_b, lamB, ZERO,
+                               ch.mat[2], ldc, nullptr)))
+                    return rc;
+                if ((rc = gemm(own, ar, br, al, ONE, gptr(a, s, x), is64(a), lda_a, 1, ch.mat[2], true, ldc, nullptr,
+                               x == 0 ? ZERO : ONE, En, ldc, lamA)))
+                    return rc;
+            }
+            s += 1;
+        }
+        const int rows = ca[s], cols = cb[s];
+        CUDA_TRY(own, launch_scale_max(En, rows, cols, ldc, ch.logacc, own->stream));
+        std::swap(E, En);
+    }
+    double2 e00;
+    double lg;
+    CUDA_TRY(own, cudaMemcpyAsync(&e00, E, sizeof e00, cudaMemcpyDeviceToHost, own->stream));
+    CUDA_TRY(own, cudaMemcpyAsync(&lg, ch.logacc, sizeof lg, cudaMemcpyDeviceToHost, own->stream));
+    CUDA_TRY(own, cudaStreamSynchronize(own->stream));
+    const double sc = std::exp(lg);
+    out[0] = e00.x * sc;
+    out[1] = e00.y * sc;
+    return PTEBD_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI ==
+extern "C" {
+
+int ptebd_required_bytes(const ptebd_config* cfg, size_t* state_bytes, size_t* workspace_bytes,
+                         size_t* workspace_min_bytes) {
+    std::string why;
+    int rc = validate_config(cfg, &why);
+    if (rc) return rc;
+    Layout L = make_layout(*cfg);
+    if (state_bytes) *state_bytes = L.state_bytes;
+    if (workspace_bytes) *workspace_bytes = ws_bytes_for(L, L.max_bonds);
+    if (workspace_min_bytes) *workspace_min_bytes = ws_bytes_for(L, 1);
+    return PTEBD_OK;
+}
+
+int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, void* workspace,
+                 size_t workspace_bytes, void* stream, ptebd_state** out) {
+    if (!out) return PTEBD_ERR_INVALID;
+    *out = nullptr;
+    std::string why;
+    int rc = validate_config(cfg, &why);
+    if (rc) return rc;
+    Layout L = make_layout(*cfg);
+    if (!state_mem || !workspace) return PTEBD_ERR_INVALID;
+    if (((uintptr_t)state_mem & 255) || ((uintptr_t)workspace & 255)) return PTEBD_ERR_MEMORY;
+    if (state_bytes < L.state_bytes) return PTEBD_ERR_MEMORY;
+    int slots = 0;
+    while (slots < L.max_bonds && ws_bytes_for(L, slots + 1) <= workspace_bytes) ++slots;
+    if (slots < 1) return PTEBD_ERR_MEMORY;
+    ptebd_state* st = new (std::nothrow) ptebd_state();
+    if (!st) return PTEBD_ERR_MEMORY;
+    st->cfg = *cfg;
+    st->L = L;
+    st->mem = static_cast<char*>(state_mem);
+    st->ws = static_cast<char*>(workspace);
+    st->ws_bytes = workspace_bytes;
+    st->slots = slots;
+    st->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&st->device);
+    cudaError_t e = cfg->precision == PTEBD_FP64 ? jacobi_prepare<double>() : jacobi_prepare<float>();
+    if (e != cudaSuccess) {
+        delete st;
+        return PTEBD_ERR_CUDA;
+    }
+    rc = ptebd_reset(st);
+    if (rc) {
+        delete st;
+        return rc;
+    }
+    *out = st;
+    return PTEBD_OK;
+}
+
+int ptebd_destroy(ptebd_state* st) {
+    if (!st) return PTEBD_ERR_INVALID;
+    delete st;
+    return PTEBD_OK;
+}
+
+int ptebd_set_stream(ptebd_state* st, void* stream) {
+    if (!st) return PTEBD_ERR_INVALID;
+    st->stream = static_cast<cudaStream_t>(stream);
+    return PTEBD_OK;
+}
+
+int ptebd_reset(ptebd_state* st) {
+    if (!st) return PTEBD_ERR_INVALID;
+    CUDA_TRY(st, cudaMemsetAsync(st->mem, 0, st->L.state_bytes, st->stream));
+    k_init_state<<<64, 256, 0, st->stream>>>(st->mem, st->L);
+    CUDA_TRY(st, cudaGetLastError());
+    st->layers = 0;
+    return PTEBD_OK;
+}
+
+const char* ptebd_last_error(const ptebd_state* st) {
+    if (!st) return "null handle";
+    return st->last_error.c_str();
+}
+
+int ptebd_get_config(const ptebd_state* st, ptebd_config* out) {
+    if (!st || !out) return PTEBD_ERR_INVALID;
+    *out = st->cfg;
+    return PTEBD_OK;
+}
+
+int ptebd_apply_layer(ptebd_state* st, const double* gates, int32_t parity, int32_t gates_on_device) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (parity != 0 && parity != 1) return set_err(st, PTEBD_ERR_INVALID, "parity must be 0 or 1");
+    const int nb = n_parity_bonds(st->L.n_sites, parity);
+    if (nb > 0 && !gates) return set_err(st, PTEBD_ERR_INVALID, "null gates");
+    int rc;
+    const double* dg = stage_gates(st, gates, nb, gates_on_device, &rc);
+    if (rc) return rc;
+    const int32_t* lists = at<int32_t>(st->mem, st->L.off_bonds);
+    rc = run(st, lists + (parity ? st->L.max_bonds : 0), nb, dg, true);
+    if (rc) return rc;
+    ++st->layers;
+    return regauge_steps(st, st->cfg.g);
+}
+
+int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds, const double* gates,
+                      int32_t gates_on_device) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (n_bonds < 0 || n_bonds > st->L.max_bonds) return set_err(st, PTEBD_ERR_INVALID, "bad bond count %d", n_bonds);
+    if (n_bonds == 0) { ++st->layers; return regauge_steps(st, st->cfg.g); }
+    if (!bonds || !gates) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    std::vector<int32_t> sorted(bonds, bonds + n_bonds);
+    std::sort(sorted.begin(), sorted.end());
+    for (int i = 0; i < n_bonds; ++i) {
+        if (sorted[i] < 0 || sorted[i] > st->L.n_sites - 2)
+            return set_err(st, PTEBD_ERR_INVALID, "bond %d out of range", sorted[i]);
+        if (i && sorted[i] - sorted[i - 1] < 2)
+            return set_err(st, PTEBD_ERR_OVERLAP, "bonds %d and %d share a site", sorted[i - 1], sorted[i]);
+    }
+    int32_t* dl = at<int32_t>(st->mem, st->L.off_bonds) + 2 * st->L.max_bonds;
+    CUDA_TRY(st, cudaMemcpyAsync(dl, bonds, (size_t)n_bonds * sizeof(int32_t), cudaMemcpyHostToDevice, st->stream));
+    int rc;
+    const double* dg = stage_gates(st, gates, n_bonds, gates_on_device, &rc);
+    if (rc) return rc;
+    rc = run(st, dl, n_bonds, dg, true);
+    if (rc) return rc;
+    ++st->layers;
+    return regauge_steps(st, st->cfg.g);
+}
+
+int ptebd_regauge(ptebd_state* st, int32_t g) {
+    if (!st || g < 0) return set_err(st, PTEBD_ERR_INVALID, "bad argument");
+    return regauge_steps(st, g);
+}
+
+int ptebd_sync(ptebd_state* st) {
+    if (!st) return PTEBD_ERR_INVALID;
+    return sync_and_check(st);
+}
+
+int ptebd_norm(ptebd_state* st, double* out) {
+    if (!st || !out) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    double v[2];
+    rc = contract(st, st, -1, -1, nullptr, v);
+    if (rc) return rc;
+    *out = std::sqrt(std::max(v[0], 0.0));
+    return PTEBD_OK;
+}
+
+int ptebd_overlap(ptebd_state* a, ptebd_state* b, double out[2]) {
+    if (!a || !b || !out) return set_err(a, PTEBD_ERR_INVALID, "null argument");
+    if (a->L.n_sites != b->L.n_sites) return set_err(a, PTEBD_ERR_INVALID, "different n_sites");
+    if (a->L.chip != b->L.chip) return set_err(a, PTEBD_ERR_INVALID, "overlap needs equal chi_max padding");
+    int rc = sync_and_check(a);
+    if (rc) return rc;
+    if ((rc = sync_and_check(b))) return rc;
+    return contract(a, b, -1, -1, nullptr, out);
+}
+
+int ptebd_expect(ptebd_state* st, int32_t site, const double* op, double out[2]) {
+    if (!st || !op || !out) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    if (site < 0 || site >= st->L.n_sites) return set_err(st, PTEBD_ERR_INVALID, "site out of range");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    double num[2], den[2];
+    if ((rc = contract(st, st, site, -1, op, num))) return rc;
+    if ((rc = contract(st, st, -1, -1, nullptr, den))) return rc;
+    out[0] = num[0] / den[0];
+    out[1] = num[1] / den[0];
+    return PTEBD_OK;
+}
+
+int ptebd_expect2(ptebd_state* st, int32_t site, const double* op, double out[2]) {
+    if (!st || !op || !out) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    if (site < 0 || site >= st->L.n_sites - 1) return set_err(st, PTEBD_ERR_INVALID, "site out of range");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    double num[2], den[2];
+    if ((rc = contract(st, st, -1, site, op, num))) return rc;
+    if ((rc = contract(st, st, -1, -1, nullptr, den))) return rc;
+    out[0] = num[0] / den[0];
+    out[1] = num[1] / den[0];
+    return PTEBD_OK;
+}
+
+int ptebd_get_chi(ptebd_state* st, int32_t* chi_out) {
+    if (!st || !chi_out) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    std::vector<int32_t> chi = host_chi(st, &rc);
+    if (rc) return rc;
+    for (int b = 0; b < st->L.n_sites - 1; ++b) chi_out[b] = chi[b + 1];
+    return PTEBD_OK;
+}
+
+int ptebd_get_lambda(ptebd_state* st, int32_t bond, double* out, int32_t* k) {
+    if (!st || !out) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    if (bond < 0 || bond > st->L.n_sites - 2) return set_err(st, PTEBD_ERR_INVALID, "bond out of range");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    int32_t kk;
+    CUDA_TRY(st, cudaMemcpyAsync(&kk, at<int32_t>(st->mem, st->L.off_chi) + bond + 1, sizeof kk, cudaMemcpyDeviceToHost,
+                                 st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    CUDA_TRY(st, cudaMemcpyAsync(out, lam_ptr(st, bond), (size_t)kk * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (k) *k = kk;
+    return PTEBD_OK;
+}
+
+int ptebd_get_site(ptebd_state* st, int32_t site, int32_t* chi_l, int32_t* chi_r, double* gamma_out) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (site < 0 || site >= st->L.n_sites) return set_err(st, PTEBD_ERR_INVALID, "site out of range");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    std::vector<int32_t> chi = host_chi(st, &rc);
+    if (rc) return rc;
+    const int cl = chi[site], cr = chi[site + 1];
+    if (chi_l) *chi_l = cl;
+    if (chi_r) *chi_r = cr;
+    if (!gamma_out) return PTEBD_OK;
+    const size_t chip = (size_t)st->L.chip, slice = chip * chip;
+    const size_t elem = st->L.elem;
+    std::vector<char> raw(2 * slice * elem);
+    CUDA_TRY(st, cudaMemcpyAsync(raw.data(), st->mem + st->L.off_gamma + (size_t)site * 2 * slice * elem, raw.size(),
+                                 cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    for (int s = 0; s < 2; ++s)
+        for (int a = 0; a < cl; ++a)
+            for (int b = 0; b < cr; ++b) {
+                const size_t src = s * slice + (size_t)b * chip + a;
+                const size_t dst = ((size_t)s * cl + a) * cr + b;
+                if (elem == sizeof(double2)) {
+                    const double2 v = reinterpret_cast<const double2*>(raw.data())[src];
+                    gamma_out[2 * dst] = v.x; gamma_out[2 * dst + 1] = v.y;
+                } else {
+                    const float2 v = reinterpret_cast<const float2*>(raw.data())[src];
+                    gamma_out[2 * dst] = v.x; gamma_out[2 * dst + 1] = v.y;
+                }
+            }
+    return PTEBD_OK;
+}
+
+int ptebd_set_lambda(ptebd_state* st, int32_t bond, int32_t k, const double* values) {
+    if (!st || !values) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    if (bond < 0 || bond > st->L.n_sites - 2) return set_err(st, PTEBD_ERR_INVALID, "bond out of range");
+    if (k < 1 || k > st->L.chi_max) return set_err(st, PTEBD_ERR_INVALID, "k out of range");
+    std::vector<double> row((size_t)st->L.chip, 0.0);
+    std::copy(values, values + k, row.begin());
+    CUDA_TRY(st, cudaMemcpyAsync(const_cast<double*>(lam_ptr(st, bond)), row.data(), row.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, st->stream));
+    CUDA_TRY(st, cudaMemcpyAsync(at<int32_t>(st->mem, st->L.off_chi) + bond + 1, &k, sizeof k, cudaMemcpyHostToDevice,
+                                 st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    return PTEBD_OK;
+}
+
+int ptebd_set_site(ptebd_state* st, int32_t site, int32_t chi_l, int32_t chi_r, const double* gamma) {
+    if (!st || !gamma) return set_err(st, PTEBD_ERR_INVALID, "null argument");
+    if (site < 0 || site >= st->L.n_sites) return set_err(st, PTEBD_ERR_INVALID, "site out of range");
+    int rc;
+    std::vector<int32_t> chi = host_chi(st, &rc);
+    if (rc) return rc;
+    if (chi[site] != chi_l || chi[site + 1] != chi_r)
+        return set_err(st, PTEBD_ERR_SHAPE, "site %d: got %dx%d, bonds say %dx%d", site, chi_l, chi_r, chi[site],
+                       chi[site + 1]);
+    const size_t chip = (size_t)st->L.chip, slice = chip * chip, elem = st->L.elem;
+    std::vector<char> raw(2 * slice * elem, 0);
+    for (int s = 0; s < 2; ++s)
+        for (int a = 0; a < chi_l; ++a)
+            for (int b = 0; b < chi_r; ++b) {
+                const size_t dst = s * slice + (size_t)b * chip + a;
+                const size_t src = ((size_t)s * chi_l + a) * chi_r + b;
+                if (elem == sizeof(double2))
+                    reinterpret_cast<double2*>(raw.data())[dst] = make_double2(gamma[2 * src], gamma[2 * src + 1]);
+                else
+                    reinterpret_cast<float2*>(raw.data())[dst] =
+                        make_float2((float)gamma[2 * src], (float)gamma[2 * src + 1]);
+            }
+    CUDA_TRY(st, cudaMemcpyAsync(st->mem + st->L.off_gamma + (size_t)site * 2 * slice * elem, raw.data(), raw.size(),
+                                 cudaMemcpyHostToDevice, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    return PTEBD_OK;
+}
+
+int ptebd_trunc_error(ptebd_state* st, double* eps_total, double* log_nu_total) {
+    if (!st) return PTEBD_ERR_INVALID;
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    double t[8];
+    CUDA_TRY(st, cudaMemcpyAsync(t, at<double>(st->mem, st->L.off_totals), sizeof t, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (eps_total) *eps_total = t[0];
+    if (log_nu_total) *log_nu_total = t[1];
+    return PTEBD_OK;
+}
+
+int ptebd_bond_stats(ptebd_state* st, double* eps, double* nu, int32_t* rank_in) {
+    if (!st) return PTEBD_ERR_INVALID;
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    const size_t nb = (size_t)st->L.n_sites - 1;
+    if (eps) CUDA_TRY(st, cudaMemcpyAsync(eps, at<double>(st->mem, st->L.off_bond_eps), nb * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    if (nu) CUDA_TRY(st, cudaMemcpyAsync(nu, at<double>(st->mem, st->L.off_bond_nu), nb * sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+    if (rank_in) CUDA_TRY(st, cudaMemcpyAsync(rank_in, at<int32_t>(st->mem, st->L.off_bond_rank), nb * sizeof(int32_t), cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    return PTEBD_OK;
+}
+
+int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n) {
+    if (!st || !out || n < 0) return PTEBD_ERR_INVALID;
+    unsigned long long w[4];
+    CUDA_TRY(st, cudaMemcpyAsync(w, at<double>(st->mem, st->L.off_totals) + 8, sizeof w, cudaMemcpyDeviceToHost,
+                                 st->stream));
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    for (int i = 0; i < std::min(n, 3); ++i) out[i] = w[i];
+    return PTEBD_OK;
+}
+
+int ptebd_timing(ptebd_state* st, int32_t enable) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (enable) {
+        CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+        st->ev_used = 0;
+        st->ev_kind.clear();
+    }
+    st->timing = enable != 0;
+    return PTEBD_OK;
+}
+
+int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_kinds) {
+    if (!st || n_kinds < 0) return PTEBD_ERR_INVALID;
+    CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    const int nk = std::min<int>(n_kinds, PTEBD_K_COUNT);
+    for (int k = 0; k < nk; ++k) {
+        if (ms) ms[k] = 0.0;
+        if (launches) launches[k] = 0;
+    }
+    for (size_t i = 0; i < st->ev_kind.size(); ++i) {
+        const int k = st->ev_kind[i];
+        float t = 0.f;
+        CUDA_TRY(st, cudaEventElapsedTime(&t, st->ev_pool[2 * i], st->ev_pool[2 * i + 1]));
+        if (k < nk) {
+            if (ms) ms[k] += t;
+            if (launches) launches[k] += 1;
+        }
+    }
+    return PTEBD_OK;
+}
+
+int ptebd_svd_sweeps(ptebd_state* st, int32_t* sweeps, int32_t* layers) {
+    if (!st) return PTEBD_ERR_INVALID;
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    if (sweeps) {
+        CUDA_TRY(st, cudaMemcpyAsync(sweeps, at<int32_t>(st->mem, st->L.off_bond_sweeps),
+                                     (size_t)(st->L.n_sites - 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, st->stream));
+        CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    }
+    if (layers) *layers = st->layers;
+    return PTEBD_OK;
+}
+
+}  // extern "C"

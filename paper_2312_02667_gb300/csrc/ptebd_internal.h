@@ -1,0 +1,107 @@
+// Internal declarations of libptebd: device memory layout, kernel arguments and
+// the launchers each translation unit provides.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/ptebd.h"
+
+namespace ptebd {
+
+// ---------------------------------------------------------------- complex --
+template <typename R> struct Cx;
+template <> struct Cx<float>  { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <typename R> using cx_t = typename Cx<R>::T;
+
+template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im) {
+    C c; c.x = (decltype(c.x))re; c.y = (decltype(c.y))im; return c;
+}
+
+// --------------------------------------------------------- device errors --
+// Bits of the latched device error word.
+enum : uint32_t {
+    DERR_NONFINITE = 1u,     // a non-finite singular value / norm
+    DERR_ZERO_THETA = 2u,    // theta' is zero: nothing to keep
+    DERR_EPS = 4u,           // eps_b >= 1 in absolute mode: nu undefined
+    DERR_NOT_CONVERGED = 8u, // a Jacobi SVD hit its sweep limit
+    DERR_TIMEOUT = 16u,      // a bounded wait on an mbarrier ran out
+};
+
+// ------------------------------------------------------------- layout ----
+// All device memory comes from two caller buffers.
+//
+// State buffer:
+//   gamma  : N sites x 2 (sigma) x chip x chip complex (float2 or double2),
+//            each (site, sigma) slice column-major: element (alpha, beta) at
+//            beta * chip + alpha; entries outside chi_{s-1} x chi_s are zero
+//   lam    : (N+1) x chip doubles, Lambda_b at (b+1)*chip; rows 0 and N are
+//            the boundary vectors (1, 0, ...)
+//   chi    : N+1 int32, chi_b at index b+1 (chi[0] = chi[N] = 1)
+//   bond_* : per-bond metrics (N-1 each)
+//   totals : [0] eps_total (gate updates), [1] sum ln nu, [2] eps of tSU steps,
+//            [3] layers applied; then 4 uint64 work counters
+//   err    : latched error word
+//   gates  : ceil((N-1)/2) x 32 doubles, staging of host gates
+//   bonds  : 3 lists of ceil((N-1)/2) int32: even bonds, odd bonds, user list
+//   contraction scratch: 8 chip x chip complex128 matrices
+// Workspace (per slot = one bond of a chunk):
+//   w, w0  : ldw x ldw complex each (ldw = 2 chip); w is rotated by the SVD,
+//            w0 keeps theta' (or its adjoint) for the second factor
+//   norms, sig : ldw doubles; perm : ldw int32; dims : 8 int32
+struct Layout {
+    int n_sites = 0, chi_max = 0, chip = 0, ldw = 0, precision = 0, max_bonds = 0;
+    size_t elem = 0;  // bytes of one complex element of gamma / w
+    // state offsets (bytes)
+    size_t off_gamma = 0, off_lam = 0, off_chi = 0, off_bond_eps = 0, off_bond_nu = 0,
+           off_bond_rank = 0, off_bond_sweeps = 0, off_totals = 0, off_err = 0,
+           off_gates = 0, off_bonds = 0, off_scratch = 0, state_bytes = 0;
+    // per-slot workspace (bytes)
+    size_t slot_w = 0, slot_small = 0, slot_bytes = 0;
+};
+
+Layout make_layout(const ptebd_config& cfg);
+
+// Device views handed to kernels.
+template <typename R>
+struct LayerArgs {
+    using C = cx_t<R>;
+    C* gamma; double* lam; int32_t* chi;
+    C* w; C* w0; double* norms; double* sig; int32_t* perm; int32_t* dims;
+    double* slot_eps; double* slot_lognu; int32_t* slot_sweeps;
+    const int32_t* bonds; const double* gates;  // gates == nullptr: tSU
+    int count, chip, ldw, n_sites, chi_max;
+    double thr_rel;   // relative threshold max(cutoff, floor)
+    int eps_mode, stabilise, max_sweeps;
+    double* bond_eps; double* bond_nu; int32_t* bond_rank; int32_t* bond_sweeps;
+    double* totals; uint32_t* err;
+    unsigned long long* work;  // [0] Jacobi pair-row visits, [1] theta flops, [2] rotations
+};
+
+// dims[] entries of a slot
+enum { D_CL = 0, D_CM = 1, D_CR = 2, D_TALL = 3, D_BOND = 4, D_K = 5, D_ROWS = 6, D_COLS = 7 };
+
+// ------------------------------------------------------------ launchers --
+template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
+cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
+                                int gated, double* totals, cudaStream_t s);
+template <typename R> cudaError_t jacobi_prepare();   // raises the dynamic smem limit
+size_t jacobi_smem_bytes(int precision, int ldw);
+
+// Transfer-matrix contraction.  C = rowscale o (op(A) B) o colscale * alpha + beta C,
+// all column-major; A and B are complex of type TA/TB, C is complex128.
+// opA: 0 = N, 1 = conjugate transpose.
+template <typename TA, typename TB>
+cudaError_t launch_zgemm(int m, int n, int k, double2 alpha,
+                         const TA* A, int lda, int opA, const TB* B, int ldb,
+                         const double* colscale_b, double2 beta, double2* Cm, int ldc,
+                         const double* rowscale_c, cudaStream_t s);
+cudaError_t launch_scale_max(double2* E, int rows, int cols, int ld, double* log_acc, cudaStream_t s);
+cudaError_t launch_fill_identity(double2* E, int rows, int cols, int ld, cudaStream_t s);
+
+}  // namespace ptebd

@@ -1,0 +1,368 @@
+// Batched one-sided (Hestenes) Jacobi SVD of the two-site tensors of a layer
+// (the SVD step of the TEBD procedure, Sec. II C of arXiv:2312.02667).
+//
+// One CTA per bond.  The matrix w (rows x cols, column-major, rows >= cols)
+// stays in global memory / L2; the CTA sweeps over blocks of NW columns:
+//   * block I is held in registers, one column per warp (lane l holds rows
+//     l, l+32, ...);
+//   * the intra-block pairs of I are rotated in shared memory (round-robin);
+//   * every later block J is streamed through a double-buffered shared-memory
+//     stage by TMA bulk copies (cp.async.bulk, completion on an mbarrier),
+//     rotated against I in NW rounds (warp w meets column (w + r) mod NW of J),
+//     and written back by a TMA bulk store.
+// Each sweep therefore meets every column pair once (block row-cyclic order).
+// A pair (a, b) with |a^H b| > tol ||a|| ||b|| is rotated by the 2x2 unitary that
+// diagonalises its Gram matrix; the sweeps stop when none was rotated.  On exit
+// the columns are U S (orthogonal, unsorted); their FP64 norms are the
+// singular values.
+//
+// Every wait on an mbarrier is bounded by a clock budget; a wait that runs out
+// latches DERR_TIMEOUT, drains the CTA's own copies and returns.
+#include <cmath>
+#include <type_traits>
+
+#include "ptebd_internal.h"
+
+namespace ptebd {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Bounded wait: about 2^31 SM cycles (~1 s) before giving up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const long long start = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - start > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+template <typename R> struct Eps;
+template <> struct Eps<float> { static constexpr double u = 5.9604644775390625e-08; };   // 2^-24
+template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e-16; };  // 2^-53
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Rotate the column pair (a, b) held by one warp (RPL entries per lane) if it is
+// not yet orthogonal to within tol.  Returns true if it rotated.
+template <typename R, int RPL>
+__device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R tol) {
+    R al = 0, be = 0, gr = 0, gi = 0;
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        al = fma(a[q].x, a[q].x, al); al = fma(a[q].y, a[q].y, al);
+        be = fma(b[q].x, b[q].x, be); be = fma(b[q].y, b[q].y, be);
+        gr = fma(a[q].x, b[q].x, gr); gr = fma(a[q].y, b[q].y, gr);
+        gi = fma(a[q].x, b[q].y, gi); gi = fma(-a[q].y, b[q].x, gi);
+    }
+    al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+    if (!(al > 0) || !(be > 0)) return false;
+    const R g = hypot(gr, gi);
+    if (!(g > tol * sqrt(al) * sqrt(be))) return false;
+    // real 2x2 problem [[al, g], [g, be]] after moving the phase of a^H b
+    const R zeta = (be - al) / (2 * g);
+    const R az = fabs(zeta);
+    const R root = (az < (R)1e15) ? sqrt(1 + zeta * zeta) : az;
+    R t = 1 / (az + root);
+    if (zeta < 0) t = -t;
+    const R c = 1 / sqrt(1 + t * t);
+    const R s = c * t;
+    const R er = gr / g, ei = gi / g;  // e = (a^H b) / |a^H b|
+    const R sr = s * er, si = s * ei;
+    // a' = c a - s conj(e) b ;  b' = s e a + c b
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const R ar = a[q].x, ai = a[q].y, br = b[q].x, bi = b[q].y;
+        a[q].x = c * ar - (sr * br + si * bi);
+        a[q].y = c * ai - (sr * bi - si * br);
+        b[q].x = c * br + (sr * ar - si * ai);
+        b[q].y = c * bi + (sr * ai + si * ar);
+    }
+    return true;
+}
+
+template <typename R, int NW, int RPL>
+__device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int cols, int j, unsigned char* smem) {
+    using C = cx_t<R>;
+    const int ldw = A.ldw;
+    const int mpad = ldw;  // rows per column slot in shared memory
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    C* bufJ0 = reinterpret_cast<C*>(smem);
+    C* bufJ1 = bufJ0 + NW * mpad;
+    C* bufI = bufJ1 + NW * mpad;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);
+    int* sh = reinterpret_cast<int*>(bar + 2);  // [0] rotations, [1] abort
+    C* bufJ[2] = {bufJ0, bufJ1};
+
+    const R tol = (R)(2.0 * sqrt((double)rows) * Eps<R>::u);
+    const int nb = (cols + NW - 1) / NW;
+    const uint32_t col_bytes = (uint32_t)(rows * sizeof(C));
+    uint32_t phase[2] = {0u, 0u};
+    int cur = 0;
+    int sweep = 0;
+    long long rot_total = 0;
+    bool converged = false;
+
+    auto issue_load = [&](int J, int buf) {
+        // one thread: expect the bytes, then one bulk copy per real column
+        const int c0 = J * NW;
+        const int nreal = min(NW, cols - c0);
+        mbar_expect_tx(&bar[buf], (uint32_t)nreal * col_bytes);
+        for (int c = 0; c < nreal; ++c)
+            bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)(c0 + c) * ldw, col_bytes, &bar[buf]);
+    };
+    auto abort_drain = [&](int late_buf, int pending_buf) {
+        // Called by all threads after a wait ran out: wait (bounded) once more
+        // for the copies still in flight, drain our bulk stores, latch the error.
+        if (tid == 0) {
+            mbar_wait_bounded(&bar[late_buf], phase[late_buf]);
+            if (pending_buf >= 0) mbar_wait_bounded(&bar[pending_buf], phase[pending_buf]);
+            bulk_wait_all();
+            atomicOr(A.err, DERR_TIMEOUT);
+        }
+        __syncthreads();
+    };
+
+    for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
+        if (tid == 0) sh[0] = 0;
+        __syncthreads();
+        for (int I = 0; I < nb; ++I) {
+            // all earlier bulk stores must have landed before plain loads of block I
+            if (tid == 0) { bulk_wait_all(); fence_async_global(); }
+            __syncthreads();
+            const int my_col = I * NW + warp;
+            const bool mine = my_col < cols;
+            C a[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) {
+                const int r = lane + 32 * q;
+                a[q] = (mine && r < rows) ? W[(size_t)my_col * ldw + r] : cmake<C>(0, 0);
+            }
+            // ---- intra-block pairs of I (round-robin), in shared memory
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) bufI[(size_t)warp * mpad + lane + 32 * q] = a[q];
+            __syncthreads();
+            for (int r = 0; r < NW - 1; ++r) {
+                if (warp < NW / 2) {
+                    auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (NW - 1)); };
+                    const int p = player(warp), q2 = player(NW - 1 - warp);
+                    if (I * NW + p < cols && I * NW + q2 < cols) {
+                        C x[RPL], y[RPL];
+#pragma unroll
+                        for (int q = 0; q < RPL; ++q) {
+                            x[q] = bufI[(size_t)p * mpad + lane + 32 * q];
+                            y[q] = bufI[(size_t)q2 * mpad + lane + 32 * q];
+                        }
+                        if (pair_rotate<R, RPL>(x, y, tol)) {
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) {
+                                bufI[(size_t)p * mpad + lane + 32 * q] = x[q];
+                                bufI[(size_t)q2 * mpad + lane + 32 * q] = y[q];
+                            }
+                            if (lane == 0) atomicAdd(&sh[0], 1);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) a[q] = bufI[(size_t)warp * mpad + lane + 32 * q];
+
+            // ---- cross pairs with every later block J, streamed by TMA
+            if (I + 1 < nb) {
+                if (tid == 0) issue_load(I + 1, cur);
+                for (int J = I + 1; J < nb; ++J) {
+                    const int nxt = cur ^ 1;
+                    if (J + 1 < nb && tid == 0) {
+                        bulk_wait_read_all();  // the store that last read bufJ[nxt] is done reading
+                        issue_load(J + 1, nxt);
+                    }
+                    const bool ok = mbar_wait_bounded(&bar[cur], phase[cur]);
+                    if (!ok) atomicOr(&sh[1], 1);
+                    __syncthreads();
+                    if (sh[1]) {
+                        abort_drain(cur, (J + 1 < nb) ? nxt : -1);
+                        return;
+                    }
+                    phase[cur] ^= 1u;
+                    C* buf = bufJ[cur];
+                    for (int r = 0; r < NW; ++r) {
+                        const int jc = (warp + r) & (NW - 1);
+                        if (mine && J * NW + jc < cols) {
+                            C y[RPL];
+#pragma unroll
+                            for (int q = 0; q < RPL; ++q) y[q] = buf[(size_t)jc * mpad + lane + 32 * q];
+                            if (pair_rotate<R, RPL>(a, y, tol)) {
+#pragma unroll
+                                for (int q = 0; q < RPL; ++q) buf[(size_t)jc * mpad + lane + 32 * q] = y[q];
+                                if (lane == 0) atomicAdd(&sh[0], 1);
+                            }
+                        }
+                        __syncthreads();
+                    }
+                    // write block J back
+                    fence_async_smem();
+                    __syncthreads();
+                    if (tid == 0) {
+                        const int c0 = J * NW;
+                        const int nreal = min(NW, cols - c0);
+                        for (int c = 0; c < nreal; ++c)
+                            bulk_s2g(W + (size_t)(c0 + c) * ldw, buf + (size_t)c * mpad, col_bytes);
+                        bulk_commit();
+                    }
+                    cur = nxt;
+                }
+            }
+            // write block I back
+            if (mine) {
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    const int r = lane + 32 * q;
+                    if (r < rows) W[(size_t)my_col * ldw + r] = a[q];
+                }
+            }
+            fence_async_global();
+            __syncthreads();
+        }
+        __syncthreads();
+        const int rot = sh[0];
+        rot_total += rot;
+        __syncthreads();
+        if (rot == 0) { converged = true; ++sweep; break; }
+    }
+    if (tid == 0) { bulk_wait_all(); fence_async_global(); }
+    __syncthreads();
+    if (!converged && tid == 0) atomicOr(A.err, DERR_NOT_CONVERGED);
+    if (tid == 0) {
+        A.slot_sweeps[j] = sweep;
+        atomicAdd(&A.work[0], (unsigned long long)sweep * (unsigned long long)(cols * (cols - 1) / 2) *
+                                  (unsigned long long)rows);
+        atomicAdd(&A.work[2], (unsigned long long)rot_total);
+    }
+    // FP64 column norms = singular values
+    double* nrm = A.norms + (size_t)j * ldw;
+    for (int c = warp; c < cols; c += NW) {
+        double acc = 0.0;
+        for (int r = lane; r < rows; r += 32) {
+            const C v = W[(size_t)c * ldw + r];
+            acc = fma((double)v.x, (double)v.x, acc);
+            acc = fma((double)v.y, (double)v.y, acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            const double s = sqrt(acc);
+            if (!isfinite(s)) atomicOr(A.err, DERR_NONFINITE);
+            nrm[c] = s;
+        }
+    }
+}
+
+template <typename R, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
+    using C = cx_t<R>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int j = blockIdx.x;
+    const int32_t* d = A.dims + j * 8;
+    const int rows = d[D_ROWS], cols = d[D_COLS];
+    C* W = A.w + (size_t)j * A.ldw * A.ldw;
+    // zero the three column stages (rows beyond `rows` must read as zero)
+    const size_t stage_elems = (size_t)3 * NW * A.ldw;
+    C* z = reinterpret_cast<C*>(smem);
+    for (size_t e = threadIdx.x; e < stage_elems; e += blockDim.x) z[e] = cmake<C>(0, 0);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(z + stage_elems);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        reinterpret_cast<int*>(bar + 2)[1] = 0;
+    }
+    fence_async_smem();
+    __syncthreads();
+    const int qa = (rows + 31) / 32;
+    if (qa <= 1) jacobi_body<R, NW, 1>(A, W, rows, cols, j, smem);
+    else if (qa <= 2) jacobi_body<R, NW, 2>(A, W, rows, cols, j, smem);
+    else if (qa <= 4) jacobi_body<R, NW, 4>(A, W, rows, cols, j, smem);
+    else if (qa <= 8) jacobi_body<R, NW, 8>(A, W, rows, cols, j, smem);
+    else jacobi_body<R, NW, 16>(A, W, rows, cols, j, smem);
+}
+
+template <typename R> struct JacobiNW;
+template <> struct JacobiNW<float> { static constexpr int v = 16; };
+template <> struct JacobiNW<double> { static constexpr int v = 8; };
+
+}  // namespace
+
+size_t jacobi_smem_bytes(int precision, int ldw) {
+    const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
+    const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 4 * sizeof(int);
+}
+
+template <typename R> cudaError_t jacobi_prepare() {
+    constexpr int NW = JacobiNW<R>::v;
+    const size_t need = jacobi_smem_bytes(std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED,
+                                          2 * PTEBD_CHI_LIMIT);
+    return cudaFuncSetAttribute(k_jacobi<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+}
+
+template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s) {
+    constexpr int NW = JacobiNW<R>::v;
+    const size_t smem = jacobi_smem_bytes(std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED, a.ldw);
+    k_jacobi<R, NW><<<a.count, NW * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t jacobi_prepare<float>();
+template cudaError_t jacobi_prepare<double>();
+template cudaError_t launch_jacobi<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_jacobi<double>(const LayerArgs<double>&, cudaStream_t);
+
+}  // namespace ptebd

@@ -1,0 +1,444 @@
+// Kernels of one pTEBD gate layer apart from the SVD (arXiv:2312.02667):
+//   k_theta    : two-site tensor theta = Lambda_{b-1} Gamma_b Lambda_b Gamma_{b+1} Lambda_{b+1}
+//                and theta' = U theta (Sec. II C), batched over the bonds of a layer;
+//   k_truncate : sort the singular values, keep chi' of them (projector P_b, Sec. III B),
+//                eps_b, nu_b = (1 - eps_b)^(-1/2), Lambda_b <- nu_b S (Sec. III C), in FP64;
+//   k_gamma_*  : Gamma_b <- Lambda_{b-1}^{-1} U and Gamma_{b+1} <- V^dagger Lambda_{b+1}^{-1}
+//                (Sec. II C), one factor straight from the rotated columns, the other
+//                through one complex GEMM with the kept theta';
+//   k_reduce   : deterministic per-layer sums of eps_b and ln nu_b.
+#include <cmath>
+
+#include "ptebd_internal.h"
+
+namespace ptebd {
+
+template <typename C> __device__ __forceinline__ C cz() { C c; c.x = 0; c.y = 0; return c; }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+// acc += x * y
+template <typename C> __device__ __forceinline__ void cfma(C& acc, C x, C y) {
+    acc.x = fma(x.x, y.x, acc.x); acc.x = fma(-x.y, y.y, acc.x);
+    acc.y = fma(x.x, y.y, acc.y); acc.y = fma(x.y, y.x, acc.y);
+}
+// acc += conj(x) * y
+template <typename C> __device__ __forceinline__ void cfma_cj(C& acc, C x, C y) {
+    acc.x = fma(x.x, y.x, acc.x); acc.x = fma(x.y, y.y, acc.x);
+    acc.y = fma(x.x, y.y, acc.y); acc.y = fma(-x.y, y.x, acc.y);
+}
+
+// ---------------------------------------------------------------- theta --
+// grid (ceil(chip/32), ceil(chip/32), count), 256 threads.  Each block computes
+// the 32x32 (alpha, gamma) tile of all four theta_{st} = X_s Y_t with
+// X_s = diag(Lambda_{b-1}) Gamma_b^s diag(Lambda_b), Y_t = Gamma_{b+1}^t diag(Lambda_{b+1}),
+// mixes them with the gate and writes theta' (tall: rows (s,alpha), cols (t,gamma))
+// or its adjoint (wide) into w and w0.
+template <typename R>
+__global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
+    using C = cx_t<R>;
+    const int j = blockIdx.z;
+    const int b = a.bonds[j];
+    const int chip = a.chip;
+    const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
+    const bool tall = cl >= cr;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        int32_t* d = a.dims + j * 8;
+        d[D_CL] = cl; d[D_CM] = cm; d[D_CR] = cr; d[D_TALL] = tall ? 1 : 0; d[D_BOND] = b;
+        d[D_K] = 0; d[D_ROWS] = tall ? 2 * cl : 2 * cr; d[D_COLS] = tall ? 2 * cr : 2 * cl;
+        atomicAdd(&a.work[1], 32ull * (unsigned long long)cl * (unsigned long long)cm * (unsigned long long)cr);
+    }
+    const int a0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
+    if (a0 >= cl || g0 >= cr) return;
+
+    __shared__ C xs[2][16][33];
+    __shared__ C ys[2][16][33];
+    __shared__ C ug[16];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const size_t slice = (size_t)chip * chip;
+    const C* G0 = a.gamma + (size_t)b * 2 * slice;
+    const C* G1 = a.gamma + (size_t)(b + 1) * 2 * slice;
+    const double* lL = a.lam + (size_t)b * chip;
+    const double* lM = a.lam + (size_t)(b + 1) * chip;
+    const double* lR = a.lam + (size_t)(b + 2) * chip;
+
+    C acc[2][2][2][2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) acc[s][t][i][q] = cz<C>();
+
+    for (int k0 = 0; k0 < cm; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            const int s = e >> 9, rem = e & 511, kk = rem >> 5, al = rem & 31;
+            const int alpha = a0 + al, beta = k0 + kk;
+            C v = cz<C>();
+            if (alpha < cl && beta < cm)
+                v = cscale(G0[s * slice + (size_t)beta * chip + alpha], (R)(lL[alpha] * lM[beta]));
+            xs[s][kk][al] = v;
+        }
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            const int t = e >> 9, rem = e & 511, gg = rem >> 4, kk = rem & 15;
+            const int gamma = g0 + gg, beta = k0 + kk;
+            C v = cz<C>();
+            if (gamma < cr && beta < cm)
+                v = cscale(G1[t * slice + (size_t)gamma * chip + beta], (R)lR[gamma]);
+            ys[t][kk][gg] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            C x[2][2], y[2][2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int i = 0; i < 2; ++i) x[s][i] = xs[s][kk][tx + 16 * i];
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) y[t][q] = ys[t][kk][ty + 16 * q];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) cfma(acc[s][t][i][q], x[s][i], y[t][q]);
+        }
+        __syncthreads();
+    }
+
+    if (a.gates != nullptr) {
+        if (threadIdx.x < 16) {
+            const double* gp = a.gates + (size_t)j * 32 + 2 * threadIdx.x;
+            ug[threadIdx.x] = cmake<C>(gp[0], gp[1]);
+        }
+        __syncthreads();
+    }
+    const size_t ldw = a.ldw;
+    C* W = a.w + (size_t)j * ldw * ldw;
+    C* W0 = a.w0 + (size_t)j * ldw * ldw;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int alpha = a0 + tx + 16 * i;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int gamma = g0 + ty + 16 * q;
+            if (alpha >= cl || gamma >= cr) continue;
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                for (int tp = 0; tp < 2; ++tp) {
+                    C v;
+                    if (a.gates != nullptr) {
+                        v = cz<C>();
+#pragma unroll
+                        for (int s = 0; s < 2; ++s)
+#pragma unroll
+                            for (int t = 0; t < 2; ++t)
+                                cfma(v, ug[(2 * sp + tp) * 4 + 2 * s + t], acc[s][t][i][q]);
+                    } else {
+                        v = acc[sp][tp][i][q];
+                    }
+                    const size_t r = (size_t)sp * cl + alpha, c = (size_t)tp * cr + gamma;
+                    if (tall) {
+                        W[c * ldw + r] = v; W0[c * ldw + r] = v;
+                    } else {
+                        const C vc = cconj(v);
+                        W[r * ldw + c] = vc; W0[r * ldw + c] = vc;
+                    }
+                }
+        }
+    }
+}
+
+// ------------------------------------------------------------- truncate --
+// grid (count), 512 threads.  norms[] holds the FP64 column norms of the
+// rotated matrix (= the singular values, unsorted).
+template <typename R>
+__global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
+    constexpr int NS = 512;
+    __shared__ double key[NS];
+    __shared__ int idx[NS];
+    __shared__ double red[NS];
+    __shared__ int kept_sh;
+    const int j = blockIdx.x, t = threadIdx.x;
+    int32_t* d = a.dims + j * 8;
+    const int ncols = d[D_COLS];
+    const int b = d[D_BOND];
+    const double* nrm = a.norms + (size_t)j * a.ldw;
+    key[t] = (t < ncols) ? nrm[t] : -1.0;
+    idx[t] = t;
+    __syncthreads();
+    // bitonic sort, descending by value, ascending index on ties
+    for (int size = 2; size <= NS; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int p = t ^ stride;
+            if (p > t) {
+                const bool desc = (t & size) == 0;
+                const double kt = key[t], kp = key[p];
+                const int it = idx[t], ip = idx[p];
+                const bool t_first = (kt > kp) || (kt == kp && it < ip);
+                if (desc ? !t_first : t_first) {
+                    key[t] = kp; key[p] = kt; idx[t] = ip; idx[p] = it;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const double smax = key[0];
+    if (!(smax > 0.0) || !isfinite(smax)) {
+        if (t == 0) {
+            atomicOr(a.err, isfinite(smax) ? DERR_ZERO_THETA : DERR_NONFINITE);
+            d[D_K] = 0;
+        }
+        return;
+    }
+    const double thr = a.thr_rel * smax;
+    // number above the threshold (the keys are sorted)
+    if (t == 0) kept_sh = 0;
+    __syncthreads();
+    if (t < ncols && key[t] > thr && (t + 1 == ncols || !(key[t + 1] > thr))) kept_sh = t + 1;
+    __syncthreads();
+    const int k = max(1, min(a.chi_max, kept_sh));
+    // FP64 weights: total and dropped, fixed-order tree sums
+    const double w = (t < ncols) ? key[t] * key[t] : 0.0;
+    red[t] = w;
+    __syncthreads();
+    for (int s = NS / 2; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    const double total = red[0];
+    __syncthreads();
+    red[t] = (t >= k) ? w : 0.0;
+    __syncthreads();
+    for (int s = NS / 2; s > 0; s >>= 1) {
+        if (t < s) red[t] += red[t + s];
+        __syncthreads();
+    }
+    const double dropped = red[0];
+    double eps = (a.eps_mode == PTEBD_EPS_RELATIVE) ? dropped / total : dropped;
+    double nu = 1.0;
+    if (a.stabilise) {
+        if (eps < 1.0) {
+            nu = 1.0 / sqrt(1.0 - eps);
+        } else if (t == 0) {
+            atomicOr(a.err, DERR_EPS);
+        }
+    }
+    double* lam_b = a.lam + (size_t)(b + 1) * a.chip;
+    for (int q = t; q < a.chip; q += NS) lam_b[q] = (q < k) ? nu * key[q] : 0.0;
+    if (t < k) {
+        a.sig[(size_t)j * a.ldw + t] = key[t];
+        a.perm[(size_t)j * a.ldw + t] = idx[t];
+    }
+    if (t == 0) {
+        d[D_K] = k;
+        a.chi[b + 1] = k;
+        a.slot_eps[j] = eps;
+        a.slot_lognu[j] = log(nu);
+        if (a.stabilise) {
+            a.bond_eps[b] = eps;
+            a.bond_nu[b] = nu;
+            a.bond_rank[b] = ncols;
+        }
+        a.bond_sweeps[b] = a.slot_sweeps[j];
+    }
+}
+
+// ----------------------------------------------------------- Gamma, direct --
+// The factor whose singular vectors are the rotated columns themselves:
+// tall (w = theta' = U S): Gamma_b[s](alpha, beta) = w[(s,alpha), perm beta] / (S_beta Lambda_{b-1,alpha})
+// wide (w = theta'^dag = V S): Gamma_{b+1}[t](beta, gamma) = conj(w[(t,gamma), perm beta]) / (S_beta Lambda_{b+1,gamma})
+// grid (ceil(chip*chip/256), 2, count), 256 threads; writes the whole padded slice.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
+    using C = cx_t<R>;
+    const int j = blockIdx.z, sg = blockIdx.y;
+    const int32_t* d = a.dims + j * 8;
+    const int k = d[D_K];
+    if (k == 0) return;  // error latched by k_truncate
+    const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND];
+    const bool tall = d[D_TALL] != 0;
+    const int chip = a.chip;
+    const size_t slice = (size_t)chip * chip;
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    if (e >= slice) return;
+    const int row = (int)(e % chip), col = (int)(e / chip);
+    const size_t ldw = a.ldw;
+    const C* W = a.w + (size_t)j * ldw * ldw;
+    const double* sig = a.sig + (size_t)j * ldw;
+    const int32_t* perm = a.perm + (size_t)j * ldw;
+    C v = cz<C>();
+    if (tall) {
+        // row = alpha, col = beta
+        if (col < k && row < cl) {
+            const double* lL = a.lam + (size_t)b * chip;
+            const double sc = 1.0 / (sig[col] * lL[row]);
+            v = cscale(W[(size_t)perm[col] * ldw + (size_t)sg * cl + row], (R)sc);
+        }
+        a.gamma[(size_t)b * 2 * slice + sg * slice + e] = v;
+    } else {
+        // row = beta, col = gamma
+        if (row < k && col < cr) {
+            const double* lR = a.lam + (size_t)(b + 2) * chip;
+            const double sc = 1.0 / (sig[row] * lR[col]);
+            v = cscale(cconj(W[(size_t)perm[row] * ldw + (size_t)sg * cr + col]), (R)sc);
+        }
+        a.gamma[(size_t)(b + 1) * 2 * slice + sg * slice + e] = v;
+    }
+}
+
+// ------------------------------------------------------------ Gamma, GEMM --
+// The other factor through Z[i, j] = sum_r conj(P[r, i]) Q[r, j]:
+// tall: P = w (columns perm beta), Q = w0 = theta', Z = S^2 V^dag:
+//       Gamma_{b+1}[t](beta, gamma) = Z[beta, (t,gamma)] / (S_beta^2 Lambda_{b+1,gamma})
+// wide: P = w0 = theta'^dag, Q = w (columns perm beta), Z = U S^2:
+//       Gamma_b[s](alpha, beta) = Z[(s,alpha), beta] / (S_beta^2 Lambda_{b-1,alpha})
+// grid (ceil(chip/32), ceil(chip/32), 2 count), 256 threads, 2x2 outputs per thread.
+template <typename R>
+__global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
+    using C = cx_t<R>;
+    const int j = blockIdx.z >> 1, sg = blockIdx.z & 1;
+    const int32_t* d = a.dims + j * 8;
+    const int k = d[D_K];
+    if (k == 0) return;
+    const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND], rows = d[D_ROWS];
+    const bool tall = d[D_TALL] != 0;
+    const int chip = a.chip;
+    const size_t slice = (size_t)chip * chip, ldw = a.ldw;
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    const int rlim = tall ? k : cl;   // valid target rows
+    const int clim = tall ? cr : k;   // valid target cols
+    C* G = a.gamma + (size_t)(tall ? b + 1 : b) * 2 * slice + sg * slice;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (r0 >= rlim || c0 >= clim) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int row = r0 + tx + 16 * i, col = c0 + ty + 16 * q;
+                if (row < chip && col < chip) G[(size_t)col * chip + row] = cz<C>();
+            }
+        return;
+    }
+    const C* W = a.w + (size_t)j * ldw * ldw;
+    const C* W0 = a.w0 + (size_t)j * ldw * ldw;
+    const C* P = tall ? W : W0;
+    const C* Q = tall ? W0 : W;
+    const int32_t* perm = a.perm + (size_t)j * ldw;
+    __shared__ int pcol[32], qcol[32];
+    __shared__ C ps[16][33], qs[16][33];
+    if (threadIdx.x < 32) {
+        const int row = r0 + threadIdx.x;
+        int pc = -1;
+        if (row < rlim) pc = tall ? perm[row] : sg * cl + row;
+        pcol[threadIdx.x] = pc;
+    } else if (threadIdx.x < 64) {
+        const int col = c0 + threadIdx.x - 32;
+        int qc = -1;
+        if (col < clim) qc = tall ? sg * cr + col : perm[col];
+        qcol[threadIdx.x - 32] = qc;
+    }
+    __syncthreads();
+    C acc[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[i][q] = cz<C>();
+    for (int k0 = 0; k0 < rows; k0 += 16) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int kk = e & 15, cc = e >> 4;
+            const int r = k0 + kk;
+            const int pc = pcol[cc], qc = qcol[cc];
+            ps[kk][cc] = (pc >= 0 && r < rows) ? P[(size_t)pc * ldw + r] : cz<C>();
+            qs[kk][cc] = (qc >= 0 && r < rows) ? Q[(size_t)qc * ldw + r] : cz<C>();
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            const C p0 = ps[kk][tx], p1 = ps[kk][tx + 16];
+            const C q0 = qs[kk][ty], q1 = qs[kk][ty + 16];
+            cfma_cj(acc[0][0], p0, q0); cfma_cj(acc[0][1], p0, q1);
+            cfma_cj(acc[1][0], p1, q0); cfma_cj(acc[1][1], p1, q1);
+        }
+        __syncthreads();
+    }
+    const double* sig = a.sig + (size_t)j * ldw;
+    const double* lnb = a.lam + (size_t)(tall ? b + 2 : b) * chip;  // Lambda_{b+1} or Lambda_{b-1}
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int row = r0 + tx + 16 * i, col = c0 + ty + 16 * q;
+            if (row >= chip || col >= chip) continue;
+            C v = cz<C>();
+            if (row < rlim && col < clim) {
+                const double sb = tall ? sig[row] : sig[col];
+                const double ln = tall ? lnb[col] : lnb[row];
+                v = cscale(acc[i][q], (R)(1.0 / (sb * sb * ln)));
+            }
+            G[(size_t)col * chip + row] = v;
+        }
+}
+
+// ------------------------------------------------------------ reductions --
+__global__ void __launch_bounds__(256) k_reduce_layer(const double* slot_eps, const double* slot_lognu,
+                                                      int count, int gated, double* totals) {
+    __shared__ double se[256], sl[256];
+    const int t = threadIdx.x;
+    double e = 0.0, l = 0.0;
+    for (int i = t; i < count; i += 256) { e += slot_eps[i]; l += slot_lognu[i]; }
+    se[t] = e; sl[t] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (t < s) { se[t] += se[t + s]; sl[t] += sl[t + s]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (gated) { totals[0] += se[0]; totals[1] += sl[0]; }
+        else { totals[2] += se[0]; }
+    }
+}
+
+// -------------------------------------------------------------- launchers --
+template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
+    const int tiles = (a.chip + 31) / 32;
+    dim3 grid(tiles, tiles, a.count);
+    k_theta<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s) {
+    k_truncate<R><<<a.count, 512, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s) {
+    const size_t slice = (size_t)a.chip * a.chip;
+    dim3 g1((unsigned)((slice + 255) / 256), 2, a.count);
+    k_gamma_direct<R><<<g1, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int tiles = (a.chip + 31) / 32;
+    dim3 g2(tiles, tiles, 2 * a.count);
+    k_gamma_gemm<R><<<g2, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
+                                int gated, double* totals, cudaStream_t s) {
+    k_reduce_layer<<<1, 256, 0, s>>>(slot_eps, slot_lognu, count, gated, totals);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_theta<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_theta<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_truncate<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_truncate<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_gamma<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_gamma<double>(const LayerArgs<double>&, cudaStream_t);
+
+}  // namespace ptebd

@@ -29,6 +29,7 @@ __all__ = [
     "random_mps_tensors",
     "random_one_site_op",
     "gates_to_interleaved",
+    "saturated_bond",
 ]
 
 
@@ -89,3 +90,21 @@ def gates_to_interleaved(gates: np.ndarray) -> np.ndarray:
     row-major with (re, im) interleaved: the layout the C ABI takes."""
     g = np.ascontiguousarray(np.asarray(gates, dtype=np.complex128))
     return np.ascontiguousarray(g.view(np.float64).reshape(-1))
+
+
+def saturated_bond(seed: int, chi: int) -> dict:
+    """Synthetic environment of one bond of a state saturated at chi_max = chi:
+    three descending, normalised Lambda vectors of length chi, two random
+    Gamma tensors (2, chi, chi) and a Haar gate.  Used where only the shape of
+    the work matters (timing the oracle on a sample of the bench workload)."""
+    rng = _rng(seed, 0x5A7, chi)
+
+    def lam():
+        x = np.sort(np.abs(rng.standard_normal(chi)))[::-1] + 1e-3
+        return x / np.linalg.norm(x)
+
+    def gam():
+        return (rng.standard_normal((2, chi, chi)) + 1j * rng.standard_normal((2, chi, chi))) / np.sqrt(2 * chi)
+
+    return {"lam_l": lam(), "lam_c": lam(), "lam_r": lam(), "gamma_l": gam(), "gamma_r": gam(),
+            "gate": haar_u4(rng)}

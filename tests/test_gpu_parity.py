@@ -1,0 +1,328 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the oracle.
+
+Tolerances (fixed by the target of this project): singular values normwise
+to 1e-10 * lambda_1 on the FP64 path and 1e-5 * lambda_1 on the mixed path;
+state fidelity per layer >= 1 - 1e-9 (FP64) and >= 1 - 1e-6 (mixed).
+Gauge-dependent tensors are never compared elementwise: only Lambda, chi,
+eps, nu and fidelities, which the method fixes uniquely.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import statevector as sv
+from paper_2312_02667_gb300 import inputs
+
+from gpu_helpers import compare_spectra, fidelity, load_into, mini_vidal, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+FTOL = {"fp64": 1e-9, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def ptebd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_02667_gb300 import ptebd as mod
+    return mod
+
+
+def thr(st_prec, cutoff=1e-12):
+    return max(cutoff, 1e-6) if st_prec == "mixed" else cutoff
+
+
+# ----------------------------------------------------- exact (no truncation)
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_untruncated_circuit_matches_statevector(ptebd, prec):
+    n, depth = 12, 10
+    st = ptebd.State(n, 64, prec, cutoff=1e-12)
+    psi = sv.zero_state(n)
+    for parity, bonds, gates in inputs.brickwork_circuit(3, n, depth):
+        st.apply_layer(gates, parity)
+        for b, u in zip(bonds, gates):
+            psi = sv.apply_two_qubit(psi, n, int(b), u)
+        mps = to_oracle(st)
+        f = sv.fidelity(sv.from_vidal(mps), psi)
+        assert f >= 1 - FTOL[prec], f
+        for b in range(n - 1):
+            ref = sv.schmidt_values(psi, n, b)
+            ref = ref[ref > thr(prec) * ref[0]]
+            compare_spectra(mps.lambdas[b], ref, TOL[prec], thr(prec), 64)
+    eps, lognu = st.trunc_error()
+    assert eps < 1e-10 and abs(lognu) < 1e-10
+
+
+def test_c1_config_n16_depth10_chi256(ptebd):
+    # N = 16, depth 10, chi_max = 256: no truncation, complex128, vs the 2^16 statevector
+    n, depth = 16, 10
+    st = ptebd.State(n, 256, "fp64", cutoff=1e-12)
+    psi = sv.zero_state(n)
+    for parity, bonds, gates in inputs.brickwork_circuit(0, n, depth):
+        st.apply_layer(gates, parity)
+        for b, u in zip(bonds, gates):
+            psi = sv.apply_two_qubit(psi, n, int(b), u)
+    mps = to_oracle(st)
+    assert sv.fidelity(sv.from_vidal(mps), psi) >= 1 - 1e-9
+    for b in range(n - 1):
+        ref = sv.schmidt_values(psi, n, b)
+        ref = ref[ref > 1e-12 * ref[0]]
+        compare_spectra(mps.lambdas[b], ref, 1e-10, 1e-12, 256)
+    assert oracle.distance_to_canonical(mps) < 1e-9
+
+
+# ------------------------------------------------------- one-layer parity --
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_layer_parity_n128_chi64(ptebd, prec):
+    # N = 128, depth 20, chi_max = 64: every layer of the GPU path applied to
+    # the oracle's own state before that layer, compared with the oracle's layer.
+    n, chi, depth = 128, 64, 20
+    cut = thr(prec)
+    st = ptebd.State(n, chi, prec, cutoff=1e-12)
+    ref = oracle.product_state(n)
+    worst_dev, worst_f = 0.0, 0.0
+    for layer, (parity, bonds, gates) in enumerate(inputs.brickwork_circuit(1, n, depth)):
+        load_into(st, ref)
+        st.apply_layer(gates, parity)
+        res = oracle.apply_layer(ref, gates, parity, chi, cut)
+        got = to_oracle(st)
+        eps_g, nu_g, rank_g = st.bond_stats()
+        for r in res.bonds:
+            b = r.bond
+            worst_dev = max(worst_dev, compare_spectra(got.lambdas[b], ref.lambdas[b], TOL[prec], cut, chi))
+            assert abs(eps_g[b] - r.eps) <= TOL[prec] * max(1.0, r.eps) + 1e-14
+            assert abs(nu_g[b] - r.nu) <= 2 * TOL[prec]
+            assert rank_g[b] == r.rank_in
+        f = fidelity(got, ref)
+        worst_f = max(worst_f, 1 - f)
+        assert f >= 1 - FTOL[prec], (layer, f)
+    sweeps, layers = st.svd_sweeps()
+    assert layers == depth and sweeps.max() < 40
+    print(f"{prec}: worst normwise lambda deviation {worst_dev:.2e}, worst 1-F {worst_f:.2e}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cumulative_circuit_n128_chi64(ptebd, prec):
+    n, chi, depth = 128, 64, 20
+    st = ptebd.State(n, chi, prec, cutoff=1e-12)
+    ref = oracle.product_state(n)
+    for parity, bonds, gates in inputs.brickwork_circuit(2, n, depth):
+        st.apply_layer(gates, parity)
+        oracle.apply_layer(ref, gates, parity, chi, thr(prec))
+    f = fidelity(to_oracle(st), ref)
+    # twenty truncated layers: errors add up but stay far below the truncation error
+    assert f >= 1 - 20 * FTOL[prec], f
+    e_g, l_g = st.trunc_error()
+    assert e_g > 0.0
+
+
+def test_mixed_against_fp64_on_the_gpu(ptebd):
+    n, chi, depth = 64, 32, 14
+    a = ptebd.State(n, chi, "fp64")
+    b = ptebd.State(n, chi, "mixed")
+    for parity, bonds, gates in inputs.brickwork_circuit(4, n, depth):
+        a.apply_layer(gates, parity)
+        b.apply_layer(gates, parity)
+        f = fidelity(to_oracle(a), to_oracle(b))
+        assert f >= 1 - 1e-5, f
+
+
+# --------------------------------------------------------------- regauge --
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ptsu_parity_and_theorem_4(ptebd, prec):
+    n = 12
+    mps = oracle.canonicalize(inputs.random_mps_tensors(5, n, 16))
+    cut = oracle.scale_to_unit_norm(oracle.truncate_all_bonds(mps, 8))
+    st = ptebd.State(n, 16, prec, cutoff=1e-14)
+    load_into(st, cut)
+    ref = cut.copy()
+    st.regauge(1)
+    oracle.ptsu_step(ref, 16, thr(prec, 1e-14))
+    got = to_oracle(st)
+    for b in range(n - 1):
+        compare_spectra(got.lambdas[b], ref.lambdas[b], TOL[prec], thr(prec, 1e-14), 16)
+    assert fidelity(got, cut) >= 1 - FTOL[prec]
+    st.regauge(n // 2 - 1)
+    c = oracle.distance_to_canonical(to_oracle(st))
+    assert c < (1e-10 if prec == "fp64" else 1e-5), c
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_layer_with_ptsu_g1(ptebd, prec):
+    n, chi = 40, 16
+    st = ptebd.State(n, chi, prec, g=1)
+    ref = oracle.product_state(n)
+    for parity, bonds, gates in inputs.brickwork_circuit(6, n, 10):
+        load_into(st, ref)
+        st.apply_layer(gates, parity)
+        res = oracle.apply_layer(ref, gates, parity, chi, thr(prec), g=1)
+        got = to_oracle(st)
+        for b in range(n - 1):
+            compare_spectra(got.lambdas[b], ref.lambdas[b], TOL[prec], thr(prec), chi)
+        assert fidelity(got, ref) >= 1 - FTOL[prec]
+
+
+# ---------------------------------------------------------- measurements --
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_norm_overlap_expect(ptebd, prec):
+    n, chi = 20, 16
+    st = ptebd.State(n, chi, prec)
+    st2 = ptebd.State(n, chi, prec)
+    for parity, bonds, gates in inputs.brickwork_circuit(7, n, 10):
+        st.apply_layer(gates, parity)
+    for parity, bonds, gates in inputs.brickwork_circuit(8, n, 7):
+        st2.apply_layer(gates, parity)
+    a, b = to_oracle(st), to_oracle(st2)
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert abs(st.norm() - oracle.norm(a)) < tol
+    assert abs(st.overlap(st2) - oracle.overlap(a, b)) < tol
+    op = inputs.random_one_site_op(2)
+    for j in (0, 7, n - 1):
+        assert abs(st.expect(j, op) - oracle.expect_one_site(a, j, op)) < tol
+    op2 = inputs.haar_u4(np.random.default_rng(1))
+    for j in (0, 9, n - 2):
+        assert abs(st.expect2(j, op2) - oracle.expect_two_site(a, j, op2)) < tol
+
+
+def test_norm_tracks_nu_stabilisation(ptebd):
+    # n* = n prod nu (Sec. III C): the device's running log prod nu against
+    # the state norm after a truncated layer on a canonical state
+    n = 12
+    mps = oracle.canonicalize(inputs.random_mps_tensors(9, n, 16))
+    st = ptebd.State(n, 6, "fp64")
+    load_into(st, mps)
+    parity, bonds, gates = inputs.brickwork_layer(9, n, 1)
+    st.apply_layer(gates, parity)
+    eps, lognu = st.trunc_error()
+    n_star = st.norm()
+    n_plain = n_star * np.exp(-lognu)
+    assert eps > 1e-3
+    assert 1 - np.sqrt(2 * eps) - 1e-12 <= n_plain <= 1 + 1e-12
+    assert (1 - np.sqrt(2 * eps)) * np.exp(lognu) - 1e-12 <= n_star <= np.exp(lognu) + 1e-12
+
+
+# ------------------------------------------------------- full-size sample --
+
+def test_sampled_bonds_n1024_chi256_mixed(ptebd):
+    # The bench workload (N = 1024, chi_max = 256, mixed precision, PtSU after
+    # every layer): run to saturation, then compare 16 sampled bonds of one
+    # gate layer with the oracle's single-bond update on the same inputs.
+    n, chi = 1024, 256
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=0)
+    circuit = inputs.brickwork_circuit(0, n, 11)
+    for parity, bonds, gates in circuit[:10]:
+        st.apply_layer(gates, parity)
+        st.regauge(1)
+    parity, bonds, gates = circuit[10]
+    rng = np.random.default_rng(0)
+    pick = sorted(rng.choice(len(bonds), 16, replace=False))
+    pick[0] = 0  # the open boundary bond
+    before = {}
+    for j in pick:
+        b = int(bonds[j])
+        before[j] = (st.lam(b - 1) if b > 0 else np.ones(1), st.site(b), st.lam(b), st.site(b + 1),
+                     st.lam(b + 1) if b + 1 < n - 1 else np.ones(1))
+    st.apply_layer(gates, parity)
+    eps_g, nu_g, _ = st.bond_stats()
+    assert st.chi().max() == chi  # saturated
+    for j in pick:
+        b = int(bonds[j])
+        ll, gb, lb, gb1, lr = before[j]
+        mini = mini_vidal(ll, gb, lb, gb1, lr)
+        r = oracle.update_bond(mini, 1, gates[j], chi, thr("mixed"))
+        lam_g = st.lam(b)
+        compare_spectra(lam_g, mini.lambdas[1], TOL["mixed"], thr("mixed"), chi)
+        assert abs(eps_g[b] - r.eps) <= 1e-5 * max(r.eps, 1e-3)
+        got = mini_vidal(ll, st.site(b), lam_g, st.site(b + 1), lr)
+        th_g = oracle.two_site_tensor(got, 1).reshape(-1)
+        th_o = oracle.two_site_tensor(mini, 1).reshape(-1)
+        f = abs(np.vdot(th_o, th_g)) ** 2 / (np.vdot(th_o, th_o).real * np.vdot(th_g, th_g).real)
+        assert f >= 1 - FTOL["mixed"], (b, f)
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_edge_cases(ptebd):
+    # two sites, one bond; parity 1 has no bonds at all
+    st = ptebd.State(2, 4, "fp64")
+    u = inputs.haar_u4(np.random.default_rng(3))
+    st.apply_layer(u[None], 0)
+    st.apply_layer(np.zeros((0, 4, 4), complex), 1)
+    ref = oracle.product_state(2)
+    oracle.apply_layer(ref, [u], 0, 4, 1e-12)
+    compare_spectra(st.lam(0), ref.lambdas[0], 1e-12, 1e-12, 4)
+    # chi_max = 1: every gated bond is cut back to a product state
+    n = 9
+    st = ptebd.State(n, 1, "fp64")
+    ref = oracle.product_state(n)
+    for parity, bonds, gates in inputs.brickwork_circuit(5, n, 4):
+        st.apply_layer(gates, parity)
+        oracle.apply_layer(ref, gates, parity, 1, 1e-12)
+    assert (st.chi() == 1).all()
+    assert fidelity(to_oracle(st), ref) >= 1 - 1e-9
+    # overlapping bonds, bad parity, out-of-range bond
+    st = ptebd.State(8, 4, "fp64")
+    with pytest.raises(ptebd.PtebdError) as e:
+        st.apply_bonds([2, 3], np.stack([u, u]))
+    assert e.value.code == -5
+    with pytest.raises(ptebd.PtebdError) as e:
+        ptebd.ptebd_apply_layer(st.handle, np.stack([u] * 4), 2)
+    assert e.value.code == -1
+    with pytest.raises(ptebd.PtebdError):
+        st.apply_bonds([7], u[None])
+    # an empty sparse layer is a no-op; reset goes back to |0...0>
+    st.apply_bonds([], np.zeros((0, 4, 4), complex))
+    st.apply_bonds([1, 4], np.stack([u, u]))
+    assert st.chi()[1] > 1
+    st.reset()
+    assert (st.chi() == 1).all() and abs(st.norm() - 1) < 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chunked_workspace_is_bit_identical(ptebd, prec):
+    n, chi = 33, 16
+    full = ptebd.State(n, chi, prec)
+    small = ptebd.State(n, chi, prec, workspace_bytes=1)  # one bond per chunk
+    assert small.workspace_bytes < full.workspace_bytes
+    for parity, bonds, gates in inputs.brickwork_circuit(11, n, 9):
+        full.apply_layer(gates, parity)
+        small.apply_layer(gates, parity)
+    for s in range(n):
+        assert np.array_equal(full.site(s), small.site(s))
+    for b in range(n - 1):
+        assert np.array_equal(full.lam(b), small.lam(b))
+
+
+def test_sparse_bonds_match_oracle(ptebd):
+    n, chi = 14, 16
+    st = ptebd.State(n, chi, "fp64")
+    ref = oracle.product_state(n)
+    rng = np.random.default_rng(12)
+    for layer in range(12):
+        bonds = sorted(rng.choice(np.arange(0, n - 1, 3), 3, replace=False) + (layer % 3))
+        bonds = [b for b in bonds if b <= n - 2]
+        gates = np.stack([inputs.haar_u4(rng) for _ in bonds])
+        st.apply_bonds(bonds, gates)
+        oracle.apply_bonds(ref, bonds, gates, chi, 1e-12)
+    got = to_oracle(st)
+    for b in range(n - 1):
+        compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-10, 1e-12, chi)
+    assert fidelity(got, ref) >= 1 - 1e-9
+
+
+def test_device_gates(ptebd):
+    import torch
+    n, chi = 20, 8
+    a = ptebd.State(n, chi, "mixed")
+    b = ptebd.State(n, chi, "mixed")
+    for parity, bonds, gates in inputs.brickwork_circuit(13, n, 6):
+        a.apply_layer(gates, parity)
+        b.apply_layer(torch.from_numpy(gates).to("cuda"), parity)
+    for s in range(n):
+        assert np.array_equal(a.site(s), b.site(s))

@@ -270,7 +270,6 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             e2e["value"] = gated_all / t_e2e
 
-    sweeps, _ = st.svd_sweeps()
     result = {
         "metric": METRIC,
         "value": value,
@@ -298,7 +297,9 @@ def run_ours(args, rank, world, local_rank):
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kern.items()},
         "event_overhead_ms_per_step": (ms_total - total_kernel_ms) / args.steps,
-        "svd_sweeps_mean_last": float(np.mean(sweeps[sweeps > 0])) if (sweeps > 0).any() else 0.0,
+        "svd_sweeps_mean": (w1[3] - w0[3]) / max(1, w1[4] - w0[4]),
+        "svds_per_step": (w1[4] - w0[4]) / args.steps,
+        "jacobi_rotations_per_step": (w1[2] - w0[2]) / args.steps,
         "roofline": {
             "kernel": "k_jacobi (one-sided Jacobi SVD)",
             "bound": "alu",

@@ -180,7 +180,8 @@ int ptebd_svd_sweeps(ptebd_state* st, int32_t* sweeps, int32_t* layers);
 #define PTEBD_K_TRUNCATE 2  /* sort, projector P_b, eps_b, nu_b, Lambda_b */
 #define PTEBD_K_GAMMA 3     /* Gamma_b and Gamma_{b+1} rebuild */
 #define PTEBD_K_REDUCE 4    /* per-layer eps / ln nu sums */
-#define PTEBD_K_COUNT 5
+#define PTEBD_K_FACTOR 5    /* tSU: X factor and theta^dag U_X */
+#define PTEBD_K_COUNT 6
 int ptebd_timing(ptebd_state* st, int32_t enable);
 int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_kinds);
 
@@ -191,7 +192,9 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  *          complex rotation of two entries);
  * out[1] = sum over every theta' of 32 chi_{b-1} chi_b chi_{b+1} (the real
  *          flops of the four complex products X_s Y_t);
- * out[2] = Jacobi rotations actually applied.  n entries are written (<= 3). */
+ * out[2] = Jacobi rotations actually applied;
+ * out[3] = Jacobi sweeps summed over every SVD; out[4] = number of SVDs.
+ * n entries are written (<= 5). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
 
 #ifdef __cplusplus

@@ -65,7 +65,7 @@ Layout make_layout(const ptebd_config& cfg) {
     L.off_bond_nu = o; o = align256(o + N * sizeof(double));
     L.off_bond_rank = o; o = align256(o + N * sizeof(int32_t));
     L.off_bond_sweeps = o; o = align256(o + N * sizeof(int32_t));
-    L.off_totals = o; o = align256(o + 8 * sizeof(double) + 4 * sizeof(unsigned long long));
+    L.off_totals = o; o = align256(o + 8 * sizeof(double) + 8 * sizeof(unsigned long long));
     L.off_err = o; o = align256(o + sizeof(uint32_t));
     L.off_gates = o; o = align256(o + nb * 32 * sizeof(double));
     L.off_bonds = o; o = align256(o + 3 * nb * sizeof(int32_t));
@@ -75,7 +75,7 @@ Layout make_layout(const ptebd_config& cfg) {
     L.slot_w = align256(ldw * ldw * L.elem);
     L.slot_small = 2 * ldw * sizeof(double) + ldw * sizeof(int32_t) + 8 * sizeof(int32_t) + 2 * sizeof(double) +
                    sizeof(int32_t);
-    L.slot_bytes = 2 * L.slot_w + L.slot_small;
+    L.slot_bytes = 3 * L.slot_w + L.slot_small;
     return L;
 }
 
@@ -85,7 +85,7 @@ namespace {
 
 // Workspace regions for `slots` slots.
 struct WsView {
-    void* w; void* w0; double* norms; double* sig; int32_t* perm; int32_t* dims;
+    void* w; void* w0; void* w1; double* norms; double* sig; int32_t* perm; int32_t* dims;
     double* slot_eps; double* slot_lognu; int32_t* slot_sweeps; size_t bytes;
 };
 
@@ -95,6 +95,7 @@ WsView ws_view(const Layout& L, char* base, int slots) {
     size_t o = 0;
     v.w = base + o; o = align256(o + s * L.slot_w);
     v.w0 = base + o; o = align256(o + s * L.slot_w);
+    v.w1 = base + o; o = align256(o + s * L.slot_w);
     v.norms = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
     v.sig = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
     v.perm = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * ldw * sizeof(int32_t));
@@ -210,6 +211,9 @@ int run_bonds(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_g
     a.chi = at<int32_t>(m, L.off_chi);
     a.w = reinterpret_cast<cx_t<R>*>(ws.w);
     a.w0 = reinterpret_cast<cx_t<R>*>(ws.w0);
+    a.w1 = reinterpret_cast<cx_t<R>*>(ws.w1);
+    a.mode = gated ? 0 : 1;
+    a.pass = 0;
     a.norms = ws.norms; a.sig = ws.sig; a.perm = ws.perm; a.dims = ws.dims;
     a.slot_eps = ws.slot_eps; a.slot_lognu = ws.slot_lognu; a.slot_sweeps = ws.slot_sweeps;
     a.chip = L.chip; a.ldw = L.ldw; a.n_sites = L.n_sites; a.chi_max = L.chi_max;
@@ -230,9 +234,23 @@ int run_bonds(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_g
         a.bonds = d_bonds + c0;
         a.gates = gated ? d_gates + (size_t)c0 * 32 : nullptr;
         CUDA_TRY(st, timed(st, PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
-        CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
-        CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
-        CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
+        if (gated) {
+            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
+        } else {
+            // tSU: SVD of theta = X Y through its rank-chi_b factors
+            LayerArgs<R> x = a;
+            x.pass = 1;
+            LayerArgs<R> y = a;
+            y.w = a.w1;
+            CUDA_TRY(st, timed(st, PTEBD_K_FACTOR, [&] { return launch_xform<R>(x, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(x, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_FACTOR, [&] { return launch_proj<R>(x, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(y, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(y, s); }));
+            CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(y, s); }));
+        }
         CUDA_TRY(st, timed(st, PTEBD_K_REDUCE, [&] {
                      return launch_reduce_layer(a.slot_eps, a.slot_lognu, a.count, gated ? 1 : 0, a.totals, s);
                  }));
@@ -761,11 +779,11 @@ int ptebd_bond_stats(ptebd_state* st, double* eps, double* nu, int32_t* rank_in)
 
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n) {
     if (!st || !out || n < 0) return PTEBD_ERR_INVALID;
-    unsigned long long w[4];
+    unsigned long long w[8];
     CUDA_TRY(st, cudaMemcpyAsync(w, at<double>(st->mem, st->L.off_totals) + 8, sizeof w, cudaMemcpyDeviceToHost,
                                  st->stream));
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
-    for (int i = 0; i < std::min(n, 3); ++i) out[i] = w[i];
+    for (int i = 0; i < std::min(n, 5); ++i) out[i] = w[i];
     return PTEBD_OK;
 }
 

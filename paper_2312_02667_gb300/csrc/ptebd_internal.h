@@ -48,8 +48,9 @@ enum : uint32_t {
 //   bonds  : 3 lists of ceil((N-1)/2) int32: even bonds, odd bonds, user list
 //   contraction scratch: 8 chip x chip complex128 matrices
 // Workspace (per slot = one bond of a chunk):
-//   w, w0  : ldw x ldw complex each (ldw = 2 chip); w is rotated by the SVD,
-//            w0 keeps theta' (or its adjoint) for the second factor
+//   w, w0, w1 : ldw x ldw complex each (ldw = 2 chip); w is rotated by the SVD,
+//            w0 keeps theta' (or its adjoint) for the second factor, w1 holds
+//            the second matrix of the tSU factorisation
 //   norms, sig : ldw doubles; perm : ldw int32; dims : 8 int32
 struct Layout {
     int n_sites = 0, chi_max = 0, chip = 0, ldw = 0, precision = 0, max_bonds = 0;
@@ -69,15 +70,18 @@ template <typename R>
 struct LayerArgs {
     using C = cx_t<R>;
     C* gamma; double* lam; int32_t* chi;
-    C* w; C* w0; double* norms; double* sig; int32_t* perm; int32_t* dims;
+    C* w; C* w0; C* w1; double* norms; double* sig; int32_t* perm; int32_t* dims;
     double* slot_eps; double* slot_lognu; int32_t* slot_sweeps;
     const int32_t* bonds; const double* gates;  // gates == nullptr: tSU
     int count, chip, ldw, n_sites, chi_max;
     double thr_rel;   // relative threshold max(cutoff, floor)
     int eps_mode, stabilise, max_sweeps;
+    int mode;         // 0: gated bond; 1: tSU through the rank-chi_b factorisation
+    int pass;         // Jacobi: 0 = rows/cols from dims, 1 = the X factor (2 chi_{b-1} x chi_b)
     double* bond_eps; double* bond_nu; int32_t* bond_rank; int32_t* bond_sweeps;
     double* totals; uint32_t* err;
-    unsigned long long* work;  // [0] Jacobi pair-row visits, [1] theta flops, [2] rotations
+    unsigned long long* work;  // [0] Jacobi pair-row visits, [1] theta flops, [2] rotations,
+                               // [3] sweeps summed, [4] SVDs
 };
 
 // dims[] entries of a slot
@@ -88,6 +92,8 @@ template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream
 template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s);
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
                                 int gated, double* totals, cudaStream_t s);
 template <typename R> cudaError_t jacobi_prepare();   // raises the dynamic smem limit

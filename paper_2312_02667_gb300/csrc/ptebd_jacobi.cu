@@ -80,9 +80,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
+// Unit roundoff and the rotation threshold factor: a pair is rotated when
+// |a^H b| > k sqrt(rows) u ||a|| ||b||.  Rounding alone leaves |a^H b| of about
+// sqrt(rows) u ||a|| ||b|| after a rotation, so the factor must sit well above 1
+// or rounding keeps re-triggering rotations (more sweeps, and every extra
+// rotation adds rounding error to the columns).
 template <typename R> struct Eps;
-template <> struct Eps<float> { static constexpr double u = 5.9604644775390625e-08; };   // 2^-24
-template <> struct Eps<double> { static constexpr double u = 1.1102230246251565e-16; };  // 2^-53
+template <> struct Eps<float> {
+    static constexpr double u = 5.9604644775390625e-08;  // 2^-24
+    static constexpr double k = 8.0;
+};
+template <> struct Eps<double> {
+    static constexpr double u = 1.1102230246251565e-16;  // 2^-53
+    static constexpr double k = 4.0;
+};
 
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
@@ -142,7 +153,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     int* sh = reinterpret_cast<int*>(bar + 2);  // [0] rotations, [1] abort
     C* bufJ[2] = {bufJ0, bufJ1};
 
-    const R tol = (R)(2.0 * sqrt((double)rows) * Eps<R>::u);
+    const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
     const int nb = (cols + NW - 1) / NW;
     const uint32_t col_bytes = (uint32_t)(rows * sizeof(C));
     uint32_t phase[2] = {0u, 0u};
@@ -286,6 +297,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         atomicAdd(&A.work[0], (unsigned long long)sweep * (unsigned long long)(cols * (cols - 1) / 2) *
                                   (unsigned long long)rows);
         atomicAdd(&A.work[2], (unsigned long long)rot_total);
+        atomicAdd(&A.work[3], (unsigned long long)sweep);
+        atomicAdd(&A.work[4], 1ull);
     }
     // FP64 column norms = singular values
     double* nrm = A.norms + (size_t)j * ldw;
@@ -311,7 +324,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int j = blockIdx.x;
     const int32_t* d = A.dims + j * 8;
-    const int rows = d[D_ROWS], cols = d[D_COLS];
+    const int rows = A.pass == 1 ? 2 * d[D_CL] : d[D_ROWS];
+    const int cols = A.pass == 1 ? d[D_CM] : d[D_COLS];
     C* W = A.w + (size_t)j * A.ldw * A.ldw;
     // zero the three column stages (rows beyond `rows` must read as zero)
     const size_t stage_elems = (size_t)3 * NW * A.ldw;

@@ -40,11 +40,14 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     const int b = a.bonds[j];
     const int chip = a.chip;
     const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
-    const bool tall = cl >= cr;
+    // tSU (mode 1) always stores theta^dag: its SVD goes through the factors
+    const bool tall = a.mode == 0 && cl >= cr;
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         int32_t* d = a.dims + j * 8;
         d[D_CL] = cl; d[D_CM] = cm; d[D_CR] = cr; d[D_TALL] = tall ? 1 : 0; d[D_BOND] = b;
-        d[D_K] = 0; d[D_ROWS] = tall ? 2 * cl : 2 * cr; d[D_COLS] = tall ? 2 * cr : 2 * cl;
+        d[D_K] = 0;
+        if (a.mode == 0) { d[D_ROWS] = tall ? 2 * cl : 2 * cr; d[D_COLS] = tall ? 2 * cr : 2 * cl; }
+        else { d[D_ROWS] = 2 * cr; d[D_COLS] = cm; }
         atomicAdd(&a.work[1], 32ull * (unsigned long long)cl * (unsigned long long)cm * (unsigned long long)cr);
     }
     const int a0 = blockIdx.x * 32, g0 = blockIdx.y * 32;
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
                         W[c * ldw + r] = v; W0[c * ldw + r] = v;
                     } else {
                         const C vc = cconj(v);
-                        W[r * ldw + c] = vc; W0[r * ldw + c] = vc;
+                        if (a.mode == 0) W[r * ldw + c] = vc;
+                        W0[r * ldw + c] = vc;
                     }
                 }
         }
@@ -387,6 +391,85 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
         }
 }
 
+// ------------------------------------------------------- tSU factors ----
+// For tSU the two-site tensor is theta = X Y with X = diag(Lambda_{b-1}) Gamma_b diag(Lambda_b)
+// (2 chi_{b-1} x chi_b, rows (s, alpha)), so rank(theta) <= chi_b.  Its SVD is taken
+// in two tall, narrow steps: X's columns are orthogonalised (X J = U_X Sigma_X), then
+// M^dag = theta^dag U_X (2 chi_{b+1} x chi_b) is orthogonalised; its rotated columns
+// are V S of theta, because theta = U_X M exactly.
+// k_xform writes X into w; grid (ceil(2 chip * chip / 256), count).
+template <typename R>
+__global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
+    using C = cx_t<R>;
+    const int j = blockIdx.y;
+    const int32_t* d = a.dims + j * 8;
+    const int cl = d[D_CL], cm = d[D_CM], b = d[D_BOND];
+    const int chip = a.chip;
+    const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
+    const int rows = 2 * cl;
+    const int r = (int)(e % (2 * chip)), beta = (int)(e / (2 * chip));
+    if (beta >= cm || r >= rows) return;
+    const int s = r / cl, alpha = r - s * cl;
+    const size_t slice = (size_t)chip * chip;
+    const C g = a.gamma[(size_t)b * 2 * slice + s * slice + (size_t)beta * chip + alpha];
+    const double sc = a.lam[(size_t)b * chip + alpha] * a.lam[(size_t)(b + 1) * chip + beta];
+    a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, (R)sc);
+}
+
+// w1 = w0 w diag(1 / sigma_X) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and
+// w = U_X Sigma_X (2 chi_{b-1} x chi_b): w1 = theta^dag U_X = M^dag.
+// grid (ceil(2 chip / 32), ceil(chip / 32), count), 256 threads.
+template <typename R>
+__global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
+    using C = cx_t<R>;
+    const int j = blockIdx.z;
+    const int32_t* d = a.dims + j * 8;
+    const int cl = d[D_CL], cm = d[D_CM], cr = d[D_CR];
+    const int rows = 2 * cr, kdim = 2 * cl;
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    if (r0 >= rows || c0 >= cm) return;
+    const size_t ldw = a.ldw;
+    const C* A = a.w0 + (size_t)j * ldw * ldw;  // rows x kdim
+    const C* B = a.w + (size_t)j * ldw * ldw;   // kdim x cm
+    C* out = a.w1 + (size_t)j * ldw * ldw;
+    const double* sig = a.norms + (size_t)j * ldw;
+    __shared__ C as[16][33], bs[16][33];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    C acc[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[i][q] = cz<C>();
+    for (int k0 = 0; k0 < kdim; k0 += 16) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int rr = e & 31, kk = e >> 5;
+            const int gr = r0 + rr, gk = k0 + kk;
+            as[kk][rr] = (gr < rows && gk < kdim) ? A[(size_t)gk * ldw + gr] : cz<C>();
+            const int kb = e & 15, cc = e >> 4;
+            const int gc = c0 + cc, gkb = k0 + kb;
+            bs[kb][cc] = (gc < cm && gkb < kdim) ? B[(size_t)gc * ldw + gkb] : cz<C>();
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            const C x0 = as[kk][tx], x1 = as[kk][tx + 16];
+            const C y0 = bs[kk][ty], y1 = bs[kk][ty + 16];
+            cfma(acc[0][0], x0, y0); cfma(acc[0][1], x0, y1);
+            cfma(acc[1][0], x1, y0); cfma(acc[1][1], x1, y1);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int gr = r0 + tx + 16 * i, gc = c0 + ty + 16 * q;
+            if (gr >= rows || gc >= cm) continue;
+            const double sg = sig[gc];
+            out[(size_t)gc * ldw + gr] = (sg > 0.0) ? cscale(acc[i][q], (R)(1.0 / sg)) : cz<C>();
+        }
+}
+
 // ------------------------------------------------------------ reductions --
 __global__ void __launch_bounds__(256) k_reduce_layer(const double* slot_eps, const double* slot_lognu,
                                                       int count, int gated, double* totals) {
@@ -428,6 +511,17 @@ template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream
     k_gamma_gemm<R><<<g2, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
+template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s) {
+    const size_t n = (size_t)2 * a.chip * a.chip;
+    dim3 grid((unsigned)((n + 255) / 256), a.count);
+    k_xform<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
+    dim3 grid((2 * a.chip + 31) / 32, (a.chip + 31) / 32, a.count);
+    k_proj<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
                                 int gated, double* totals, cudaStream_t s) {
     k_reduce_layer<<<1, 256, 0, s>>>(slot_eps, slot_lognu, count, gated, totals);
@@ -440,5 +534,9 @@ template cudaError_t launch_truncate<float>(const LayerArgs<float>&, cudaStream_
 template cudaError_t launch_truncate<double>(const LayerArgs<double>&, cudaStream_t);
 template cudaError_t launch_gamma<float>(const LayerArgs<float>&, cudaStream_t);
 template cudaError_t launch_gamma<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_xform<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_xform<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_proj<float>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_proj<double>(const LayerArgs<double>&, cudaStream_t);
 
 }  // namespace ptebd

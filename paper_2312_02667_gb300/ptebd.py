@@ -37,7 +37,7 @@ EXPORTS = (
     "ptebd_bond_stats", "ptebd_svd_sweeps", "ptebd_timing", "ptebd_timing_read",
     "ptebd_work_counters",
 )
-KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce")
+KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
 
 class ptebd_config(ctypes.Structure):
@@ -292,9 +292,10 @@ def ptebd_timing_read(h):
 
 
 def ptebd_work_counters(h):
-    """(Jacobi pair-row visits, theta flops, rotations applied) since create/reset."""
-    out = np.zeros(3, dtype=np.uint64)
-    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 3), h)
+    """(Jacobi pair-row visits, theta flops, rotations applied, sweeps summed,
+    SVDs) since create/reset."""
+    out = np.zeros(5, dtype=np.uint64)
+    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 5), h)
     return tuple(int(x) for x in out)
 
 

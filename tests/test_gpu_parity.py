@@ -194,7 +194,7 @@ def test_norm_tracks_nu_stabilisation(ptebd):
     # n* = n prod nu (Sec. III C): the device's running log prod nu against
     # the state norm after a truncated layer on a canonical state
     n = 12
-    mps = oracle.canonicalize(inputs.random_mps_tensors(9, n, 16))
+    mps = oracle.canonicalize(inputs.random_mps_tensors(9, n, 6))
     st = ptebd.State(n, 6, "fp64")
     load_into(st, mps)
     parity, bonds, gates = inputs.brickwork_layer(9, n, 1)

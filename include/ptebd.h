@@ -197,6 +197,45 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  * n entries are written (<= 5). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
 
+/* Batched serving of independent states (many circuits with uneven N,
+ * chi_max and precision): ptebd_batch_create groups n distinct states, which
+ * must outlive the batch.  ptebd_batch_apply_layer applies to every state i
+ * one layer of parity parities[i] with gates[i] (host memory, or device memory
+ * when gates_on_device != NULL and gates_on_device[i] != 0; parity -1 leaves
+ * state i untouched in this call, for circuits of uneven depth), followed by that
+ * state's g PtSU steps: the same work as ptebd_apply_layer, recorded as
+ * parallel branches of one CUDA graph (one graph per parity pattern, cached by
+ * the batch) so that small states run side by side.  Asynchronous: every
+ * state's stream waits for the graph; errors latched on the device are
+ * reported by each state's next synchronising call. */
+typedef struct ptebd_batch ptebd_batch;
+int ptebd_batch_create(ptebd_state* const* states, int32_t n, ptebd_batch** out);
+int ptebd_batch_destroy(ptebd_batch* b);
+const char* ptebd_batch_last_error(const ptebd_batch* b);
+int ptebd_batch_apply_layer(ptebd_batch* b, const double* const* gates, const int32_t* parities,
+                            const int32_t* gates_on_device);
+
+/* Batched SVD with the layer's one-sided Jacobi kernel (the SVD step of the
+ * TEBD procedure, Sec. II C, on caller matrices; used for SVD-only
+ * benchmarks and tests).
+ * precision: PTEBD_FP64 (complex128 matrices) or PTEBD_MIXED (complex64).
+ * a: device memory, `batch` matrices of rows x cols, column-major, leading
+ *    dimension lda >= rows, matrix i at element offset i * lda * cols;
+ *    requires cols <= rows <= 2 * PTEBD_CHI_LIMIT and rows even.
+ * sigma: device, batch x cols doubles, the singular values of each matrix in
+ *    descending order (FP64 norms of the rotated columns).
+ * u: device or NULL; when given, batch x (ldu x cols) complex of the input
+ *    type, column k = the left singular vector of sigma[k] (zero if sigma[k] = 0).
+ * workspace: device, 256-byte aligned, at least ptebd_svd_workspace_bytes.
+ * The input is not modified.  Runs on `stream` (cudaStream_t).  check != 0
+ * synchronises the stream and reports device errors (sweep limit, non-finite
+ * values, a wait that ran out); check == 0 returns at once. */
+int ptebd_svd_workspace_bytes(int32_t precision, int32_t batch, int32_t rows, int32_t cols,
+                              size_t* bytes);
+int ptebd_svd_batched(int32_t precision, int32_t batch, int32_t rows, int32_t cols,
+                      const void* a, int32_t lda, double* sigma, void* u, int32_t ldu,
+                      void* workspace, size_t workspace_bytes, void* stream, int32_t check);
+
 #ifdef __cplusplus
 }
 #endif

@@ -235,6 +235,15 @@ def _site_matrix(mps: Vidal, s: int) -> np.ndarray:
     return mps.gammas[s] * mps.lam(s)[None, None, :]
 
 
+def _transfer(e: np.ndarray, ma: np.ndarray, mb: np.ndarray) -> np.ndarray:
+    """E' = sum_s M_a[s]^dag E M_b[s]: one step of the left-to-right transfer
+    matrices, written as the two matrix products per physical index."""
+    out = np.zeros((ma.shape[2], mb.shape[2]), dtype=np.complex128)
+    for s in range(ma.shape[0]):
+        out += ma[s].conj().T @ (e @ mb[s])
+    return out
+
+
 def overlap(a: Vidal, b: Vidal) -> complex:
     """<a|b> by left-to-right transfer matrices (Eq. of the MPS decomposition,
     Sec. II A)."""
@@ -242,8 +251,7 @@ def overlap(a: Vidal, b: Vidal) -> complex:
         raise OracleError("different lengths")
     e = np.ones((1, 1), dtype=np.complex128)
     for s in range(a.n_sites):
-        ma, mb = _site_matrix(a, s), _site_matrix(b, s)
-        e = np.einsum("sai,ab,sbj->ij", ma.conj(), e, mb)
+        e = _transfer(e, _site_matrix(a, s), _site_matrix(b, s))
     return complex(e[0, 0])
 
 
@@ -259,9 +267,11 @@ def expect_one_site(mps: Vidal, site: int, op: np.ndarray) -> complex:
     for s in range(mps.n_sites):
         m = _site_matrix(mps, s)
         if s == site:
-            e = np.einsum("xai,ab,xy,ybj->ij", m.conj(), e, op, m)
+            # sum_{x,y} O[x,y] M[x]^dag E M[y]
+            me = np.einsum("xy,yab->xab", op, m)
+            e = _transfer(e, m, me)
         else:
-            e = np.einsum("sai,ab,sbj->ij", m.conj(), e, m)
+            e = _transfer(e, m, m)
     return complex(e[0, 0]) / overlap(mps, mps)
 
 
@@ -273,12 +283,13 @@ def expect_two_site(mps: Vidal, site: int, op: np.ndarray) -> complex:
     while s < mps.n_sites:
         if s == site:
             m1, m2 = _site_matrix(mps, s), _site_matrix(mps, s + 1)
-            pair = np.einsum("xab,ybc->xyac", m1, m2)
-            e = np.einsum("xyai,ab,xyst,stbj->ij", pair.conj(), e, op, pair)
+            pair = np.einsum("xab,ybc->xyac", m1, m2).reshape(4, m1.shape[1], m2.shape[2])
+            opair = np.einsum("ij,jac->iac", op.reshape(4, 4), pair)
+            e = _transfer(e, pair, opair)
             s += 2
         else:
             m = _site_matrix(mps, s)
-            e = np.einsum("sai,ab,sbj->ij", m.conj(), e, m)
+            e = _transfer(e, m, m)
             s += 1
     return complex(e[0, 0]) / overlap(mps, mps)
 

@@ -469,7 +469,35 @@ int contract(ptebd_state* a, ptebd_state* b, int site1, int site2, const double*
     return PTEBD_OK;
 }
 
+// Launch sequence of one gate layer on `st` (gates already staged in the
+// state's own device buffer), on whatever stream st->stream currently is.
+int layer_launches(ptebd_state* st, int parity) {
+    const int nb = n_parity_bonds(st->L.n_sites, parity);
+    const int32_t* lists = at<int32_t>(st->mem, st->L.off_bonds);
+    const double* dg = at<double>(st->mem, st->L.off_gates);
+    int rc = run(st, lists + (parity ? st->L.max_bonds : 0), nb, dg, true);
+    if (rc) return rc;
+    return regauge_steps(st, st->cfg.g);
+}
+
 }  // namespace
+
+// A set of independent states whose layers are launched together: one CUDA
+// graph per parity pattern, each state a parallel branch on its own stream.
+struct ptebd_batch {
+    std::vector<ptebd_state*> states;
+    cudaStream_t capture = nullptr;            // capture stream (owned)
+    std::vector<cudaStream_t> branch;          // one per state (owned)
+    std::vector<cudaEvent_t> ev;               // fork / join events (owned)
+    std::vector<std::pair<std::vector<int32_t>, cudaGraphExec_t>> cache;
+    std::string last_error;
+    ~ptebd_batch() {
+        for (auto& c : cache) cudaGraphExecDestroy(c.second);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaStream_t s : branch) cudaStreamDestroy(s);
+        if (capture) cudaStreamDestroy(capture);
+    }
+};
 
 // =================================================================== ABI ==
 extern "C" {
@@ -814,6 +842,120 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
             if (ms) ms[k] += t;
             if (launches) launches[k] += 1;
         }
+    }
+    return PTEBD_OK;
+}
+
+int ptebd_batch_create(ptebd_state* const* states, int32_t n, ptebd_batch** out) {
+    if (!out || !states || n < 1) return PTEBD_ERR_INVALID;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!states[i]) return PTEBD_ERR_INVALID;
+        for (int k = 0; k < i; ++k)
+            if (states[k] == states[i]) return PTEBD_ERR_INVALID;  // a state appears once
+    }
+    ptebd_batch* b = new (std::nothrow) ptebd_batch();
+    if (!b) return PTEBD_ERR_MEMORY;
+    b->states.assign(states, states + n);
+    bool ok = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking) == cudaSuccess;
+    b->branch.resize(n, nullptr);
+    b->ev.resize(n + 1, nullptr);
+    for (int i = 0; ok && i < n; ++i) ok = cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i <= n; ++i) ok = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        delete b;
+        return PTEBD_ERR_CUDA;
+    }
+    *out = b;
+    return PTEBD_OK;
+}
+
+int ptebd_batch_destroy(ptebd_batch* b) {
+    if (!b) return PTEBD_ERR_INVALID;
+    cudaStreamSynchronize(b->capture);
+    delete b;
+    return PTEBD_OK;
+}
+
+const char* ptebd_batch_last_error(const ptebd_batch* b) { return b ? b->last_error.c_str() : "null batch"; }
+
+int ptebd_batch_apply_layer(ptebd_batch* b, const double* const* gates, const int32_t* parities,
+                            const int32_t* gates_on_device) {
+    if (!b || !parities) return PTEBD_ERR_INVALID;
+    const int n = (int)b->states.size();
+    std::vector<int32_t> key(parities, parities + n);
+    for (int i = 0; i < n; ++i) {
+        if (key[i] < -1 || key[i] > 1) { b->last_error = "parity must be -1, 0 or 1"; return PTEBD_ERR_INVALID; }
+        if (key[i] >= 0 && n_parity_bonds(b->states[i]->L.n_sites, key[i]) > 0 && (!gates || !gates[i])) {
+            b->last_error = "null gates";
+            return PTEBD_ERR_INVALID;
+        }
+    }
+    // 1. the branches start after all earlier work of every state; gates are
+    //    staged into each state's own buffer (fixed addresses: the graph is reused)
+    for (int i = 0; i < n; ++i) {
+        ptebd_state* st = b->states[i];
+        const int nb = key[i] >= 0 ? n_parity_bonds(st->L.n_sites, key[i]) : 0;
+        if (nb > 0) {
+            const cudaMemcpyKind kind = (gates_on_device && gates_on_device[i]) ? cudaMemcpyDeviceToDevice
+                                                                                 : cudaMemcpyHostToDevice;
+            if (cudaMemcpyAsync(at<double>(st->mem, st->L.off_gates), gates[i], (size_t)nb * 32 * sizeof(double), kind,
+                                st->stream) != cudaSuccess) {
+                b->last_error = "gate staging failed";
+                return PTEBD_ERR_CUDA;
+            }
+        }
+        if (cudaEventRecord(b->ev[i], st->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(b->capture, b->ev[i], 0) != cudaSuccess) {
+            b->last_error = "event failed";
+            return PTEBD_ERR_CUDA;
+        }
+    }
+    // 2. the graph of this parity pattern (recorded once)
+    cudaGraphExec_t exec = nullptr;
+    for (auto& c : b->cache)
+        if (c.first == key) exec = c.second;
+    if (!exec) {
+        cudaStream_t cap;
+        if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PTEBD_ERR_CUDA;
+        int rc = PTEBD_OK;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+        if (!rc && cudaEventRecord(b->ev[n], cap) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+        for (int i = 0; !rc && i < n; ++i) {
+            ptebd_state* st = b->states[i];
+            const cudaStream_t saved = st->stream;
+            const bool timing = st->timing;
+            st->timing = false;
+            st->stream = b->branch[i];
+            if (cudaStreamWaitEvent(b->branch[i], b->ev[n], 0) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+            if (!rc && key[i] >= 0) rc = layer_launches(st, key[i]);
+            if (!rc && cudaEventRecord(b->ev[i], b->branch[i]) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+            if (!rc && cudaStreamWaitEvent(cap, b->ev[i], 0) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+            st->stream = saved;
+            st->timing = timing;
+        }
+        const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+        if (!rc && ee != cudaSuccess) rc = PTEBD_ERR_CUDA;
+        if (!rc && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (rc) {
+            b->last_error = "recording the batch graph failed";
+            return rc;
+        }
+        b->cache.emplace_back(key, exec);
+    }
+    // 3. launch; every state's stream waits for the graph
+    if (cudaGraphLaunch(exec, b->capture) != cudaSuccess) {
+        b->last_error = "graph launch failed";
+        return PTEBD_ERR_CUDA;
+    }
+    if (cudaEventRecord(b->ev[n], b->capture) != cudaSuccess) return PTEBD_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+        ptebd_state* st = b->states[i];
+        if (cudaStreamWaitEvent(st->stream, b->ev[n], 0) != cudaSuccess) return PTEBD_ERR_CUDA;
+        if (key[i] >= 0) ++st->layers;
     }
     return PTEBD_OK;
 }

@@ -40,6 +40,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -71,11 +74,14 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Bounded wait: about 2^31 SM cycles (~1 s) before giving up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: about 2^31 SM cycles (~1 s) before giving up, or at once when
+// another warp of the CTA has already given up (abort flag set).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  const volatile int* abort_flag = nullptr) {
     const long long start = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - start > (1ll << 31)) return false;
+        if (abort_flag && *abort_flag) return false;
     }
     return true;
 }
@@ -116,26 +122,31 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     }
     al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
     if (!(al > 0) || !(be > 0)) return false;
-    const R g = hypot(gr, gi);
+    const R g = sqrt(gr * gr + gi * gi);
     if (!(g > tol * sqrt(al) * sqrt(be))) return false;
     // real 2x2 problem [[al, g], [g, be]] after moving the phase of a^H b
-    const R zeta = (be - al) / (2 * g);
+    const R ig = 1 / g;
+    const R zeta = (be - al) * (ig * (R)0.5);
     const R az = fabs(zeta);
     const R root = (az < (R)1e15) ? sqrt(1 + zeta * zeta) : az;
     R t = 1 / (az + root);
     if (zeta < 0) t = -t;
-    const R c = 1 / sqrt(1 + t * t);
-    const R s = c * t;
-    const R er = gr / g, ei = gi / g;  // e = (a^H b) / |a^H b|
-    const R sr = s * er, si = s * ei;
+    // c = 1/sqrt(1+t^2) is applied as 1 + (c - 1) with c - 1 in closed form:
+    // for t^2 below the unit roundoff c itself rounds to 1 while s = t does
+    // not, and every such rotation would scale the pair's norm by
+    // sqrt(1 + t^2) > 1 (a systematic growth of all singular values).
+    const R r1 = sqrt(1 + t * t);
+    const R cm1 = -(t * t) / (r1 * (1 + r1));
+    const R s = t / r1;
+    const R sr = s * gr * ig, si = s * gi * ig;  // s e, e = (a^H b) / |a^H b|
     // a' = c a - s conj(e) b ;  b' = s e a + c b
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
         const R ar = a[q].x, ai = a[q].y, br = b[q].x, bi = b[q].y;
-        a[q].x = c * ar - (sr * br + si * bi);
-        a[q].y = c * ai - (sr * bi - si * br);
-        b[q].x = c * br + (sr * ar - si * ai);
-        b[q].y = c * bi + (sr * ai + si * ar);
+        a[q].x = ar + (cm1 * ar - (sr * br + si * bi));
+        a[q].y = ai + (cm1 * ai - (sr * bi - si * br));
+        b[q].x = br + (cm1 * br + (sr * ar - si * ai));
+        b[q].y = bi + (cm1 * bi + (sr * ai + si * ar));
     }
     return true;
 }
@@ -149,8 +160,9 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     C* bufJ0 = reinterpret_cast<C*>(smem);
     C* bufJ1 = bufJ0 + NW * mpad;
     C* bufI = bufJ1 + NW * mpad;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);
-    int* sh = reinterpret_cast<int*>(bar + 2);  // [0] rotations, [1] abort
+    uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);  // [2]: TMA loads of the J stages
+    uint64_t* sbar = bar + 2;                                        // [2][NW]: per-slot hand-offs
+    int* sh = reinterpret_cast<int*>(sbar + 2 * NW);                  // [0] rotations, [1] abort
     C* bufJ[2] = {bufJ0, bufJ1};
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
@@ -236,17 +248,16 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         bulk_wait_read_all();  // the store that last read bufJ[nxt] is done reading
                         issue_load(J + 1, nxt);
                     }
-                    const bool ok = mbar_wait_bounded(&bar[cur], phase[cur]);
-                    if (!ok) atomicOr(&sh[1], 1);
-                    __syncthreads();
-                    if (sh[1]) {
-                        abort_drain(cur, (J + 1 < nb) ? nxt : -1);
-                        return;
-                    }
-                    phase[cur] ^= 1u;
+                    // Round r: warp w meets column (w + r) mod NW of the stage.  A column
+                    // passes from warp w+1 (round r-1) to warp w (round r) through its
+                    // slot barrier, so warps only wait for their one predecessor.
+                    bool ok = mbar_wait_bounded(&bar[cur], phase[cur], &sh[1]);
                     C* buf = bufJ[cur];
-                    for (int r = 0; r < NW; ++r) {
+                    uint64_t* sb = sbar + cur * NW;
+                    for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
+                        if (r > 0) ok = mbar_wait_bounded(&sb[jc], (uint32_t)((r - 1) & 1), &sh[1]);
+                        if (!ok) break;
                         if (mine && J * NW + jc < cols) {
                             C y[RPL];
 #pragma unroll
@@ -257,11 +268,18 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                                 if (lane == 0) atomicAdd(&sh[0], 1);
                             }
                         }
-                        __syncthreads();
+                        __syncwarp();
+                        mbar_arrive(&sb[jc]);
                     }
+                    if (!ok) atomicOr(&sh[1], 1);
+                    phase[cur] ^= 1u;
                     // write block J back
                     fence_async_smem();
                     __syncthreads();
+                    if (sh[1]) {
+                        abort_drain(cur, (J + 1 < nb) ? nxt : -1);
+                        return;
+                    }
                     if (tid == 0) {
                         const int c0 = J * NW;
                         const int nreal = min(NW, cols - c0);
@@ -335,8 +353,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
+        for (int i = 0; i < 2 * NW; ++i) mbar_init(&bar[2 + i], 32);  // one arrival per lane
         mbar_init_fence();
-        reinterpret_cast<int*>(bar + 2)[1] = 0;
+        reinterpret_cast<int*>(bar + 2 + 2 * NW)[1] = 0;
     }
     fence_async_smem();
     __syncthreads();
@@ -357,7 +376,7 @@ template <> struct JacobiNW<double> { static constexpr int v = 8; };
 size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
-    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 4 * sizeof(int);
+    return (size_t)3 * nw * ldw * elem + (2 + 2 * nw) * sizeof(uint64_t) + 4 * sizeof(int);
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

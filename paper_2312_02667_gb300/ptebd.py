@@ -35,7 +35,8 @@ EXPORTS = (
     "ptebd_sync", "ptebd_norm", "ptebd_overlap", "ptebd_expect", "ptebd_expect2", "ptebd_get_chi",
     "ptebd_get_lambda", "ptebd_get_site", "ptebd_set_lambda", "ptebd_set_site", "ptebd_trunc_error",
     "ptebd_bond_stats", "ptebd_svd_sweeps", "ptebd_timing", "ptebd_timing_read",
-    "ptebd_work_counters",
+    "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
+    "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
@@ -86,6 +87,12 @@ _SIGS = {
     "ptebd_timing": (_P, ctypes.c_int32),
     "ptebd_timing_read": (_P, _D, _I, ctypes.c_int32),
     "ptebd_work_counters": (_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32),
+    "ptebd_svd_workspace_bytes": (ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _SZ),
+    "ptebd_svd_batched": (ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                          _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P, ctypes.c_int32),
+    "ptebd_batch_create": (ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)),
+    "ptebd_batch_destroy": (_P,),
+    "ptebd_batch_apply_layer": (_P, ctypes.POINTER(_D), _I, _I),
 }
 
 
@@ -99,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.restype = ctypes.c_int
     lib.ptebd_last_error.argtypes = [_P]
     lib.ptebd_last_error.restype = ctypes.c_char_p
+    lib.ptebd_batch_last_error.argtypes = [_P]
+    lib.ptebd_batch_last_error.restype = ctypes.c_char_p
     return lib
 
 
@@ -297,6 +306,94 @@ def ptebd_work_counters(h):
     out = np.zeros(5, dtype=np.uint64)
     _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 5), h)
     return tuple(int(x) for x in out)
+
+
+def ptebd_svd_workspace_bytes(precision, batch, rows, cols) -> int:
+    out = ctypes.c_size_t()
+    _check(lib.ptebd_svd_workspace_bytes(int(precision), int(batch), int(rows), int(cols), ctypes.byref(out)))
+    return out.value
+
+
+def ptebd_svd_batched(precision, batch, rows, cols, a_ptr, lda, sigma_ptr, u_ptr, ldu, ws_ptr, ws_bytes, stream,
+                      check=1):
+    _check(lib.ptebd_svd_batched(int(precision), int(batch), int(rows), int(cols), _P(a_ptr), int(lda),
+                                 _P(sigma_ptr), _P(u_ptr) if u_ptr else None, int(ldu), _P(ws_ptr), int(ws_bytes),
+                                 _P(stream), int(check)))
+
+
+def svd_batched(a, want_u=False, check=True):
+    """Singular values (descending) and optionally left singular vectors of a
+    batch of complex matrices: a torch tensor (batch, rows, cols) of
+    complex64 or complex128 on the GPU.  Returns (sigma, u) tensors."""
+    import torch
+    if a.dtype not in (torch.complex64, torch.complex128) or not a.is_cuda or a.dim() != 3:
+        raise TypeError("a must be a (batch, rows, cols) complex CUDA tensor")
+    prec = PTEBD_FP64 if a.dtype == torch.complex128 else PTEBD_MIXED
+    batch, rows, cols = a.shape
+    am = a.transpose(1, 2).contiguous()  # column-major per matrix
+    sigma = torch.empty((batch, cols), dtype=torch.float64, device=a.device)
+    u = torch.empty((batch, cols, rows), dtype=a.dtype, device=a.device) if want_u else None
+    wb = ptebd_svd_workspace_bytes(prec, batch, rows, cols)
+    ws = torch.empty(wb, dtype=torch.uint8, device=a.device)
+    ptebd_svd_batched(prec, batch, rows, cols, am.data_ptr(), rows, sigma.data_ptr(),
+                      u.data_ptr() if u is not None else 0, rows, ws.data_ptr(), wb,
+                      torch.cuda.current_stream(a.device).cuda_stream, 1 if check else 0)
+    return sigma, (u.transpose(1, 2) if u is not None else None)
+
+
+def ptebd_batch_create(handles):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    out = _P()
+    _check(lib.ptebd_batch_create(arr, len(handles), ctypes.byref(out)))
+    return out
+
+
+def ptebd_batch_destroy(b):
+    _check(lib.ptebd_batch_destroy(b))
+
+
+def ptebd_batch_last_error(b) -> str:
+    return lib.ptebd_batch_last_error(b).decode()
+
+
+def ptebd_batch_apply_layer(b, gates_list, parities):
+    """gates_list[i]: (n_i, 4, 4) complex host array or CUDA tensor for state i."""
+    n = len(parities)
+    keep = []
+    ptrs = (_D * n)()
+    dev = np.zeros(n, dtype=np.int32)
+    for i, g in enumerate(gates_list):
+        p, d, k = _gates_arg(g)
+        ptrs[i] = p
+        dev[i] = d
+        keep.append(k)
+    par = np.ascontiguousarray(np.asarray(parities, dtype=np.int32))
+    rc = lib.ptebd_batch_apply_layer(b, ptrs, _iptr(par), _iptr(dev))
+    if rc != PTEBD_OK:
+        raise PtebdError(rc, lib.ptebd_batch_last_error(b).decode())
+    return keep
+
+
+class Batch:
+    """Independent states advanced together (one CUDA graph per parity pattern)."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        self.handle = ptebd_batch_create([s.handle for s in self.states])
+
+    def apply_layer(self, gates_list, parities):
+        self._keep = ptebd_batch_apply_layer(self.handle, gates_list, parities)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ptebd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ owner --

@@ -1,0 +1,82 @@
+"""Batched serving: many independent states advanced by one graph launch per
+layer must give exactly what the same states give one by one, and match the
+oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02667_gb300 import inputs
+
+from gpu_helpers import compare_spectra, fidelity, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptebd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_02667_gb300 import ptebd as mod
+    return mod
+
+
+def test_batch_equals_one_by_one(ptebd):
+    specs = [(10, 4, "fp64", 0), (23, 8, "mixed", 1), (40, 16, "mixed", 0), (17, 32, "fp64", 1),
+             (31, 16, "mixed", 1), (12, 8, "mixed", 0)]
+    depth = [6, 9, 7, 8, 5, 9]
+    solo = [ptebd.State(n, c, p, g=g) for n, c, p, g in specs]
+    grouped = [ptebd.State(n, c, p, g=g, workspace_bytes=1 if i % 2 else None) for i, (n, c, p, g) in enumerate(specs)]
+    circuits = [inputs.brickwork_circuit(100 + i, n, depth[i], circuit=i) for i, (n, _, _, _) in enumerate(specs)]
+    batch = ptebd.Batch(grouped)
+    for layer in range(max(depth)):
+        gl, par = [], []
+        for i in range(len(specs)):
+            if layer < depth[i]:
+                parity, bonds, gates = circuits[i][layer]
+                solo[i].apply_layer(gates, parity)
+                gl.append(gates)
+                par.append(parity)
+            else:
+                gl.append(None)
+                par.append(-1)
+        batch.apply_layer(gl, par)
+    for i, (n, _, _, _) in enumerate(specs):
+        for s in range(n):
+            assert np.array_equal(solo[i].site(s), grouped[i].site(s)), (i, s)
+        for b in range(n - 1):
+            assert np.array_equal(solo[i].lam(b), grouped[i].lam(b))
+        assert grouped[i].svd_sweeps()[1] == depth[i]
+    batch.close()
+
+
+def test_uneven_circuits_against_oracle(ptebd):
+    # a reduced version of the batched-serving workload: uneven N, depth and
+    # chi_max, Haar gates, one graph launch per layer; oracle on every circuit
+    rng = np.random.default_rng(5)
+    k = 8
+    ns = rng.integers(20, 61, k)
+    ds = rng.integers(4, 11, k)
+    chis = rng.choice([8, 16, 32], k)
+    states = [ptebd.State(int(ns[i]), int(chis[i]), "mixed") for i in range(k)]
+    refs = [oracle.product_state(int(ns[i])) for i in range(k)]
+    circuits = [inputs.brickwork_circuit(200 + i, int(ns[i]), int(ds[i]), circuit=i) for i in range(k)]
+    batch = ptebd.Batch(states)
+    for layer in range(int(ds.max())):
+        gl, par = [], []
+        for i in range(k):
+            if layer < ds[i]:
+                parity, bonds, gates = circuits[i][layer]
+                oracle.apply_layer(refs[i], gates, parity, int(chis[i]), 1e-6)
+                gl.append(gates)
+                par.append(parity)
+            else:
+                gl.append(None)
+                par.append(-1)
+        batch.apply_layer(gl, par)
+    for i in range(k):
+        got = to_oracle(states[i])
+        for b in range(int(ns[i]) - 1):
+            compare_spectra(got.lambdas[b], refs[i].lambdas[b], 1e-5, 1e-6, int(chis[i]))
+        assert fidelity(got, refs[i]) >= 1 - int(ds[i]) * 1e-6
+    batch.close()

@@ -40,8 +40,23 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void counter_release_add(int* p) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], 1;" ::"r"(smem_u32(p)) : "memory");
+}
+__device__ __forceinline__ int counter_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+// Bounded spin until *p >= target (or the CTA has aborted).
+__device__ __forceinline__ bool counter_wait_bounded(const int* p, int target, const volatile int* abort_flag) {
+    const long long start = clock64();
+    while (counter_acquire(p) < target) {
+        if (clock64() - start > (1ll << 31)) return false;
+        if (*abort_flag) return false;
+        __nanosleep(20);
+    }
+    return true;
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -161,9 +176,10 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     C* bufJ1 = bufJ0 + NW * mpad;
     C* bufI = bufJ1 + NW * mpad;
     uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);  // [2]: TMA loads of the J stages
-    uint64_t* sbar = bar + 2;                                        // [2][NW]: per-slot hand-offs
-    int* sh = reinterpret_cast<int*>(sbar + 2 * NW);                  // [0] rotations, [1] abort
+    int* sh = reinterpret_cast<int*>(bar + 2);                        // [0] rotations, [1] abort
+    int* slot_done = sh + 2;  // [2][NW]: rounds completed on each column slot of each stage
     C* bufJ[2] = {bufJ0, bufJ1};
+    int jblocks[2] = {0, 0};  // J blocks processed so far on each stage
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
     const int nb = (cols + NW - 1) / NW;
@@ -249,14 +265,17 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         issue_load(J + 1, nxt);
                     }
                     // Round r: warp w meets column (w + r) mod NW of the stage.  A column
-                    // passes from warp w+1 (round r-1) to warp w (round r) through its
-                    // slot barrier, so warps only wait for their one predecessor.
+                    // passes from warp w+1 (round r-1) to warp w (round r) through the
+                    // slot's round counter (release / acquire), so a warp only waits for
+                    // its one predecessor; the counters only grow, so a waiter can never
+                    // mistake an older round for the one it needs.
                     bool ok = mbar_wait_bounded(&bar[cur], phase[cur], &sh[1]);
                     C* buf = bufJ[cur];
-                    uint64_t* sb = sbar + cur * NW;
+                    int* done = slot_done + cur * NW;
+                    const int base = jblocks[cur] * NW;
                     for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
-                        if (r > 0) ok = mbar_wait_bounded(&sb[jc], (uint32_t)((r - 1) & 1), &sh[1]);
+                        if (r > 0) ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
                         if (!ok) break;
                         if (mine && J * NW + jc < cols) {
                             C y[RPL];
@@ -269,10 +288,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             }
                         }
                         __syncwarp();
-                        mbar_arrive(&sb[jc]);
+                        if (lane == 0) counter_release_add(&done[jc]);
                     }
                     if (!ok) atomicOr(&sh[1], 1);
                     phase[cur] ^= 1u;
+                    ++jblocks[cur];
                     // write block J back
                     fence_async_smem();
                     __syncthreads();
@@ -353,9 +373,9 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        for (int i = 0; i < 2 * NW; ++i) mbar_init(&bar[2 + i], 32);  // one arrival per lane
         mbar_init_fence();
-        reinterpret_cast<int*>(bar + 2 + 2 * NW)[1] = 0;
+        int* sh = reinterpret_cast<int*>(bar + 2);
+        for (int i = 0; i < 2 + 2 * NW; ++i) sh[i] = 0;  // rotations, abort, slot round counters
     }
     fence_async_smem();
     __syncthreads();
@@ -376,7 +396,7 @@ template <> struct JacobiNW<double> { static constexpr int v = 8; };
 size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
-    return (size_t)3 * nw * ldw * elem + (2 + 2 * nw) * sizeof(uint64_t) + 4 * sizeof(int);
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + (2 + 2 * nw) * sizeof(int);
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

@@ -298,6 +298,9 @@ def run_ours(args, rank, world, local_rank):
         "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kern.items()},
         "event_overhead_ms_per_step": (ms_total - total_kernel_ms) / args.steps,
         "svd_sweeps_mean": (w1[3] - w0[3]) / max(1, w1[4] - w0[4]),
+        "svd_sweeps_mean_gated": ((w1[3] - w0[3]) - (w1[6] - w0[6])) / max(1, (w1[4] - w0[4]) - (w1[7] - w0[7])),
+        "svd_sweeps_mean_tsu": (w1[6] - w0[6]) / max(1, w1[7] - w0[7]),
+        "jacobi_visit_share_tsu": (w1[5] - w0[5]) / max(1, w1[0] - w0[0]),
         "svds_per_step": (w1[4] - w0[4]) / args.steps,
         "jacobi_rotations_per_step": (w1[2] - w0[2]) / args.steps,
         "roofline": {

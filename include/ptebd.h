@@ -193,8 +193,9 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  * out[1] = sum over every theta' of 32 chi_{b-1} chi_b chi_{b+1} (the real
  *          flops of the four complex products X_s Y_t);
  * out[2] = Jacobi rotations actually applied;
- * out[3] = Jacobi sweeps summed over every SVD; out[4] = number of SVDs.
- * n entries are written (<= 5). */
+ * out[3] = Jacobi sweeps summed over every SVD; out[4] = number of SVDs;
+ * out[5..7] = the same three counts (visits, sweeps, SVDs) for the Jacobi runs
+ * of the tSU steps alone.  n entries are written (<= 8). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
 
 /* Batched serving of independent states (many circuits with uneven N,

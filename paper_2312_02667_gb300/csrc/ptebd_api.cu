@@ -811,7 +811,7 @@ int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n) {
     CUDA_TRY(st, cudaMemcpyAsync(w, at<double>(st->mem, st->L.off_totals) + 8, sizeof w, cudaMemcpyDeviceToHost,
                                  st->stream));
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
-    for (int i = 0; i < std::min(n, 5); ++i) out[i] = w[i];
+    for (int i = 0; i < std::min(n, 8); ++i) out[i] = w[i];
     return PTEBD_OK;
 }
 

@@ -337,6 +337,12 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         atomicAdd(&A.work[2], (unsigned long long)rot_total);
         atomicAdd(&A.work[3], (unsigned long long)sweep);
         atomicAdd(&A.work[4], 1ull);
+        if (A.mode == 1) {  // tSU factors, counted apart as well
+            atomicAdd(&A.work[5], (unsigned long long)sweep * (unsigned long long)(cols * (cols - 1) / 2) *
+                                      (unsigned long long)rows);
+            atomicAdd(&A.work[6], (unsigned long long)sweep);
+            atomicAdd(&A.work[7], 1ull);
+        }
     }
     // FP64 column norms = singular values
     double* nrm = A.norms + (size_t)j * ldw;

@@ -302,9 +302,9 @@ def ptebd_timing_read(h):
 
 def ptebd_work_counters(h):
     """(Jacobi pair-row visits, theta flops, rotations applied, sweeps summed,
-    SVDs) since create/reset."""
-    out = np.zeros(5, dtype=np.uint64)
-    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 5), h)
+    SVDs, tSU visits, tSU sweeps, tSU SVDs) since create/reset."""
+    out = np.zeros(8, dtype=np.uint64)
+    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 8), h)
     return tuple(int(x) for x in out)
 
 

@@ -12,9 +12,12 @@
 //     and written back by a TMA bulk store.
 // Each sweep therefore meets every column pair once (block row-cyclic order).
 // A pair (a, b) with |a^H b| > tol ||a|| ||b|| is rotated by the 2x2 unitary that
-// diagonalises its Gram matrix; the sweeps stop when none was rotated.  On exit
-// the columns are U S (orthogonal, unsorted); their FP64 norms are the
-// singular values.
+// diagonalises its Gram matrix; the sweeps stop when none was rotated.  The
+// squared column norms are recomputed at the start of every sweep and then
+// tracked through the rotations (a' and b' norms follow from the 2x2 problem),
+// so a pair costs one complex dot product; a norm that drops a lot is
+// recomputed from the rotated column.  On exit the columns are U S
+// (orthogonal, unsorted); their FP64 norms are the singular values.
 //
 // Every wait on an mbarrier is bounded by a clock budget; a wait that runs out
 // latches DERR_TIMEOUT, drains the CTA's own copies and returns.
@@ -123,46 +126,102 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-// Rotate the column pair (a, b) held by one warp (RPL entries per lane) if it is
-// not yet orthogonal to within tol.  Returns true if it rotated.
+// Parameters of the rotation that diagonalises [[al, g e], [g conj(e), be]]
+// (al = |a|^2, be = |b|^2, g e = a^H b): t = tan of the angle, cm1 = cos - 1,
+// (sr, si) = sin * e.  Applied as a' = a + cm1 a - s conj(e) b, b' = b + cm1 b + s e a:
+// writing cos as 1 + (cos - 1) with cos - 1 in closed form keeps the rotation norm
+// preserving when t^2 is below the unit roundoff (cos itself would round to 1 while
+// sin = t does not, and every such rotation would scale the pair by sqrt(1 + t^2)).
+template <typename R> struct RotParams { R cm1, sr, si, tg; };
+
+__device__ __forceinline__ RotParams<float> rot_params(float al, float be, float gr, float gi, float g2) {
+    // MUFU reciprocal square roots; cos is refined by one Newton step so that
+    // cos^2 (1 + t^2) = 1 to rounding (the sign of the residual is not biased).
+    const float ig = rsqrtf(g2);
+    const float g = g2 * ig;
+    const float zeta = (be - al) * (0.5f * ig);
+    const float az = fabsf(zeta);
+    const float q0 = fmaf(zeta, zeta, 1.0f);
+    const float root = az < 1e15f ? q0 * rsqrtf(q0) : az;
+    float t = __fdividef(1.0f, az + root);
+    if (zeta < 0.0f) t = -t;
+    const float q = fmaf(t, t, 1.0f);
+    float c = rsqrtf(q);
+    c = c * fmaf(-0.5f * q * c, c, 1.5f);
+    RotParams<float> p;
+    p.cm1 = __fdividef(-(t * t) * (c * c), 1.0f + c);
+    const float s = t * c;
+    p.sr = s * gr * ig;
+    p.si = s * gi * ig;
+    p.tg = t * g;
+    return p;
+}
+
+__device__ __forceinline__ RotParams<double> rot_params(double al, double be, double gr, double gi, double g2) {
+    const double g = sqrt(g2);
+    const double ig = 1.0 / g;
+    const double zeta = (be - al) * (0.5 * ig);
+    const double az = fabs(zeta);
+    const double root = az < 1e150 ? sqrt(1.0 + zeta * zeta) : az;
+    double t = 1.0 / (az + root);
+    if (zeta < 0.0) t = -t;
+    const double r1 = sqrt(1.0 + t * t);
+    RotParams<double> p;
+    p.cm1 = -(t * t) / (r1 * (1.0 + r1));
+    const double s = t / r1;
+    p.sr = s * gr * ig;
+    p.si = s * gi * ig;
+    p.tg = t * g;
+    return p;
+}
+
 template <typename R, int RPL>
-__device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R tol) {
-    R al = 0, be = 0, gr = 0, gi = 0;
+__device__ __forceinline__ R col_norm2(const cx_t<R> (&a)[RPL]) {
+    R s0 = 0, s1 = 0;
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
-        al = fma(a[q].x, a[q].x, al); al = fma(a[q].y, a[q].y, al);
-        be = fma(b[q].x, b[q].x, be); be = fma(b[q].y, b[q].y, be);
-        gr = fma(a[q].x, b[q].x, gr); gr = fma(a[q].y, b[q].y, gr);
-        gi = fma(a[q].x, b[q].y, gi); gi = fma(-a[q].y, b[q].x, gi);
+        s0 = fma(a[q].x, a[q].x, s0);
+        s1 = fma(a[q].y, a[q].y, s1);
     }
-    al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+    return warp_sum(s0 + s1);
+}
+
+// Rotate the column pair (a, b) held by one warp (RPL entries per lane) if it is
+// not yet orthogonal to within tol; al and be are their tracked squared norms and
+// are updated.  Returns true if it rotated.
+template <typename R, int RPL>
+__device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R& al, R& be, R tol2) {
+    R gr0 = 0, gr1 = 0, gi0 = 0, gi1 = 0;  // a^H b, two partial sums each
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        if (q & 1) {
+            gr1 = fma(a[q].x, b[q].x, gr1); gr1 = fma(a[q].y, b[q].y, gr1);
+            gi1 = fma(a[q].x, b[q].y, gi1); gi1 = fma(-a[q].y, b[q].x, gi1);
+        } else {
+            gr0 = fma(a[q].x, b[q].x, gr0); gr0 = fma(a[q].y, b[q].y, gr0);
+            gi0 = fma(a[q].x, b[q].y, gi0); gi0 = fma(-a[q].y, b[q].x, gi0);
+        }
+    }
+    const R gr = warp_sum(gr0 + gr1), gi = warp_sum(gi0 + gi1);
     if (!(al > 0) || !(be > 0)) return false;
-    const R g = sqrt(gr * gr + gi * gi);
-    if (!(g > tol * sqrt(al) * sqrt(be))) return false;
-    // real 2x2 problem [[al, g], [g, be]] after moving the phase of a^H b
-    const R ig = 1 / g;
-    const R zeta = (be - al) * (ig * (R)0.5);
-    const R az = fabs(zeta);
-    const R root = (az < (R)1e15) ? sqrt(1 + zeta * zeta) : az;
-    R t = 1 / (az + root);
-    if (zeta < 0) t = -t;
-    // c = 1/sqrt(1+t^2) is applied as 1 + (c - 1) with c - 1 in closed form:
-    // for t^2 below the unit roundoff c itself rounds to 1 while s = t does
-    // not, and every such rotation would scale the pair's norm by
-    // sqrt(1 + t^2) > 1 (a systematic growth of all singular values).
-    const R r1 = sqrt(1 + t * t);
-    const R cm1 = -(t * t) / (r1 * (1 + r1));
-    const R s = t / r1;
-    const R sr = s * gr * ig, si = s * gi * ig;  // s e, e = (a^H b) / |a^H b|
-    // a' = c a - s conj(e) b ;  b' = s e a + c b
+    const R g2 = gr * gr + gi * gi;
+    if (!(g2 > (tol2 * al) * be)) return false;
+    const RotParams<R> p = rot_params(al, be, gr, gi, g2);
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
         const R ar = a[q].x, ai = a[q].y, br = b[q].x, bi = b[q].y;
-        a[q].x = ar + (cm1 * ar - (sr * br + si * bi));
-        a[q].y = ai + (cm1 * ai - (sr * bi - si * br));
-        b[q].x = br + (cm1 * br + (sr * ar - si * ai));
-        b[q].y = bi + (cm1 * bi + (sr * ai + si * ar));
+        a[q].x = ar + (p.cm1 * ar - (p.sr * br + p.si * bi));
+        a[q].y = ai + (p.cm1 * ai - (p.sr * bi - p.si * br));
+        b[q].x = br + (p.cm1 * br + (p.sr * ar - p.si * ai));
+        b[q].y = bi + (p.cm1 * bi + (p.sr * ai + p.si * ar));
     }
+    // norms from the 2x2 problem; the one that shrinks is recomputed when it
+    // lost most of its size (cancellation in the update)
+    R al2 = al - p.tg, be2 = be + p.tg;
+    if (!(al2 > (R)0.125 * al)) al2 = col_norm2<R, RPL>(a);
+    if (!(be2 > (R)0.125 * be)) be2 = col_norm2<R, RPL>(b);
+    al = al2;
+    be = be2;
     return true;
 }
 
@@ -176,12 +235,16 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     C* bufJ1 = bufJ0 + NW * mpad;
     C* bufI = bufJ1 + NW * mpad;
     uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);  // [2]: TMA loads of the J stages
-    int* sh = reinterpret_cast<int*>(bar + 2);                        // [0] rotations, [1] abort
+    R* jn2 = reinterpret_cast<R*>(bar + 2);        // [2][NW]: tracked |col|^2 of the J stage slots
+    R* in2 = jn2 + 2 * NW;                          // [NW]: |col|^2 of the I block (intra phase)
+    int* sh = reinterpret_cast<int*>(in2 + NW);     // [0] rotations, [1] abort
     int* slot_done = sh + 2;  // [2][NW]: rounds completed on each column slot of each stage
     C* bufJ[2] = {bufJ0, bufJ1};
     int jblocks[2] = {0, 0};  // J blocks processed so far on each stage
+    double* nrm2 = A.norms + (size_t)j * ldw;  // squared column norms between blocks (FP64)
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
+    const R tol2 = tol * tol;
     const int nb = (cols + NW - 1) / NW;
     const uint32_t col_bytes = (uint32_t)(rows * sizeof(C));
     uint32_t phase[2] = {0u, 0u};
@@ -211,7 +274,19 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     };
 
     for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
-        if (tid == 0) sh[0] = 0;
+        if (tid == 0) { sh[0] = 0; bulk_wait_all(); fence_async_global(); }
+        __syncthreads();
+        // exact squared column norms at the start of every sweep
+        for (int c = warp; c < cols; c += NW) {
+            R s0 = 0, s1 = 0;
+            for (int r = lane; r < rows; r += 32) {
+                const C v = W[(size_t)c * ldw + r];
+                s0 = fma(v.x, v.x, s0);
+                s1 = fma(v.y, v.y, s1);
+            }
+            const R s2 = warp_sum(s0 + s1);
+            if (lane == 0) nrm2[c] = (double)s2;
+        }
         __syncthreads();
         for (int I = 0; I < nb; ++I) {
             // all earlier bulk stores must have landed before plain loads of block I
@@ -228,6 +303,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             // ---- intra-block pairs of I (round-robin), in shared memory
 #pragma unroll
             for (int q = 0; q < RPL; ++q) bufI[(size_t)warp * mpad + lane + 32 * q] = a[q];
+            if (lane == 0) in2[warp] = mine ? (R)nrm2[my_col] : (R)0;
             __syncthreads();
             for (int r = 0; r < NW - 1; ++r) {
                 if (warp < NW / 2) {
@@ -240,13 +316,19 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             x[q] = bufI[(size_t)p * mpad + lane + 32 * q];
                             y[q] = bufI[(size_t)q2 * mpad + lane + 32 * q];
                         }
-                        if (pair_rotate<R, RPL>(x, y, tol)) {
+                        R nx = in2[p], ny = in2[q2];
+                        if (pair_rotate<R, RPL>(x, y, nx, ny, tol2)) {
 #pragma unroll
                             for (int q = 0; q < RPL; ++q) {
                                 bufI[(size_t)p * mpad + lane + 32 * q] = x[q];
                                 bufI[(size_t)q2 * mpad + lane + 32 * q] = y[q];
                             }
-                            if (lane == 0) atomicAdd(&sh[0], 1);
+                            __syncwarp();
+                            if (lane == 0) {
+                                in2[p] = nx;
+                                in2[q2] = ny;
+                                atomicAdd(&sh[0], 1);
+                            }
                         }
                     }
                 }
@@ -254,6 +336,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             }
 #pragma unroll
             for (int q = 0; q < RPL; ++q) a[q] = bufI[(size_t)warp * mpad + lane + 32 * q];
+            R al = in2[warp];
 
             // ---- cross pairs with every later block J, streamed by TMA
             if (I + 1 < nb) {
@@ -268,23 +351,34 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     // passes from warp w+1 (round r-1) to warp w (round r) through the
                     // slot's round counter (release / acquire), so a warp only waits for
                     // its one predecessor; the counters only grow, so a waiter can never
-                    // mistake an older round for the one it needs.
+                    // mistake an older round for the one it needs.  The column's tracked
+                    // squared norm travels with it (global at round 0, then the stage's
+                    // slot, and back to global after the last round).
                     bool ok = mbar_wait_bounded(&bar[cur], phase[cur], &sh[1]);
                     C* buf = bufJ[cur];
                     int* done = slot_done + cur * NW;
+                    R* sn2 = jn2 + cur * NW;
                     const int base = jblocks[cur] * NW;
                     for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
+                        const int gcol = J * NW + jc;
                         if (r > 0) ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
                         if (!ok) break;
-                        if (mine && J * NW + jc < cols) {
-                            C y[RPL];
+                        if (gcol < cols) {
+                            R be = (r == 0) ? (R)nrm2[gcol] : sn2[jc];
+                            if (mine) {
+                                C y[RPL];
 #pragma unroll
-                            for (int q = 0; q < RPL; ++q) y[q] = buf[(size_t)jc * mpad + lane + 32 * q];
-                            if (pair_rotate<R, RPL>(a, y, tol)) {
+                                for (int q = 0; q < RPL; ++q) y[q] = buf[(size_t)jc * mpad + lane + 32 * q];
+                                if (pair_rotate<R, RPL>(a, y, al, be, tol2)) {
 #pragma unroll
-                                for (int q = 0; q < RPL; ++q) buf[(size_t)jc * mpad + lane + 32 * q] = y[q];
-                                if (lane == 0) atomicAdd(&sh[0], 1);
+                                    for (int q = 0; q < RPL; ++q) buf[(size_t)jc * mpad + lane + 32 * q] = y[q];
+                                    if (lane == 0) atomicAdd(&sh[0], 1);
+                                }
+                            }
+                            if (lane == 0) {
+                                sn2[jc] = be;
+                                if (r == NW - 1) nrm2[gcol] = (double)be;
                             }
                         }
                         __syncwarp();
@@ -317,6 +411,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     const int r = lane + 32 * q;
                     if (r < rows) W[(size_t)my_col * ldw + r] = a[q];
                 }
+                if (lane == 0) nrm2[my_col] = (double)al;
             }
             fence_async_global();
             __syncthreads();
@@ -380,7 +475,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init_fence();
-        int* sh = reinterpret_cast<int*>(bar + 2);
+        int* sh = reinterpret_cast<int*>(reinterpret_cast<R*>(bar + 2) + 3 * NW);
         for (int i = 0; i < 2 + 2 * NW; ++i) sh[i] = 0;  // rotations, abort, slot round counters
     }
     fence_async_smem();
@@ -402,7 +497,8 @@ template <> struct JacobiNW<double> { static constexpr int v = 8; };
 size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
-    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + (2 + 2 * nw) * sizeof(int);
+    const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (2 + 2 * nw) * sizeof(int);
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

@@ -394,12 +394,11 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
 // ------------------------------------------------------- tSU factors ----
 // For tSU the two-site tensor is theta = X Y with X = diag(Lambda_{b-1}) Gamma_b diag(Lambda_b)
 // (2 chi_{b-1} x chi_b, rows (s, alpha)), so rank(theta) <= chi_b.  Its SVD is taken
-// in two tall, narrow steps: an orthonormal basis U_X of range(X) is found by
-// orthogonalising the columns of X~ = diag(Lambda_{b-1}) Gamma_b (X without its positive
-// column scaling Lambda_b: the same range, and near the canonical form X~ is close to an
-// isometry, so its Jacobi needs few sweeps); then M^dag = theta^dag U_X (2 chi_{b+1} x
-// chi_b) is orthogonalised: its rotated columns are V S of theta, because theta = U_X M.
-// k_xform writes X~ into w; grid (ceil(2 chip * chip / 256), count).
+// in two tall, narrow steps: X's columns are orthogonalised (X J = U_X Sigma_X; the
+// graded column norms Lambda_b make this converge fast), then M^dag = theta^dag U_X
+// (2 chi_{b+1} x chi_b) is orthogonalised: its rotated columns are V S of theta,
+// because theta = U_X M exactly.
+// k_xform writes X into w; grid (ceil(2 chip * chip / 256), count).
 template <typename R>
 __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     using C = cx_t<R>;
@@ -414,12 +413,12 @@ __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     const int s = r / cl, alpha = r - s * cl;
     const size_t slice = (size_t)chip * chip;
     const C g = a.gamma[(size_t)b * 2 * slice + s * slice + (size_t)beta * chip + alpha];
-    const double sc = a.lam[(size_t)b * chip + alpha];
+    const double sc = a.lam[(size_t)b * chip + alpha] * a.lam[(size_t)(b + 1) * chip + beta];
     a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, (R)sc);
 }
 
-// w1 = w0 w diag(1 / sigma) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and
-// w = U_X diag(sigma) the rotated columns of X~ (2 chi_{b-1} x chi_b): w1 = theta^dag U_X = M^dag.
+// w1 = w0 w diag(1 / sigma_X) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and
+// w = U_X Sigma_X (2 chi_{b-1} x chi_b): w1 = theta^dag U_X = M^dag.
 // grid (ceil(2 chip / 32), ceil(chip / 32), count), 256 threads.
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {

@@ -237,6 +237,31 @@ int ptebd_svd_batched(int32_t precision, int32_t batch, int32_t rows, int32_t co
                       const void* a, int32_t lda, double* sigma, void* u, int32_t ldu,
                       void* workspace, size_t workspace_bytes, void* stream, int32_t check);
 
+/* Allocation-free variant of ptebd_svd_batched (the paper has no
+ * counterpart: this is a convenience of the library, not part of the method).
+ * Some callers cannot allocate device memory at all, for example code that a
+ * host framework hands only its input and output buffers, or code that must
+ * not call cudaMalloc / cudaFree because those calls synchronise the device or
+ * are not allowed where it runs.  This entry point takes the same arguments as
+ * ptebd_svd_batched minus the workspace and keeps its scratch in a fixed
+ * device array inside the library of PTEBD_NOALLOC_SCRATCH_BYTES bytes; every
+ * GPU that loads the library holds that array until the process exits.  It
+ * calls no allocating routine.
+ * - A batch whose scratch (ptebd_svd_workspace_bytes) exceeds the array is
+ *   rejected with PTEBD_ERR_MEMORY (e.g. at most 15 complex64 or 7 complex128
+ *   matrices of 512 x 512 per call).
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.
+ * - All calls share the array and it keeps the previous call's contents (the
+ *   parts that must start at zero are cleared on every call): calls whose
+ *   work overlaps on the GPU (two streams, two host threads) race on it and
+ *   must be serialised by the caller. */
+#define PTEBD_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int ptebd_svd_batched_noalloc(int32_t precision, int32_t batch, int32_t rows, int32_t cols,
+                              const void* a, int32_t lda, double* sigma, void* u, int32_t ldu,
+                              void* stream, int32_t check);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,6 +37,7 @@ EXPORTS = (
     "ptebd_bond_stats", "ptebd_svd_sweeps", "ptebd_timing", "ptebd_timing_read",
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
+    "ptebd_svd_batched_noalloc",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
@@ -93,6 +94,8 @@ _SIGS = {
     "ptebd_batch_create": (ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)),
     "ptebd_batch_destroy": (_P,),
     "ptebd_batch_apply_layer": (_P, ctypes.POINTER(_D), _I, _I),
+    "ptebd_svd_batched_noalloc": (ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
+                                  ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32),
 }
 
 
@@ -319,6 +322,13 @@ def ptebd_svd_batched(precision, batch, rows, cols, a_ptr, lda, sigma_ptr, u_ptr
     _check(lib.ptebd_svd_batched(int(precision), int(batch), int(rows), int(cols), _P(a_ptr), int(lda),
                                  _P(sigma_ptr), _P(u_ptr) if u_ptr else None, int(ldu), _P(ws_ptr), int(ws_bytes),
                                  _P(stream), int(check)))
+
+
+def ptebd_svd_batched_noalloc(precision, batch, rows, cols, a_ptr, lda, sigma_ptr, u_ptr, ldu, stream, check=1):
+    """The allocation-free batched SVD (scratch in the library's fixed device array)."""
+    _check(lib.ptebd_svd_batched_noalloc(int(precision), int(batch), int(rows), int(cols), _P(a_ptr), int(lda),
+                                         _P(sigma_ptr), _P(u_ptr) if u_ptr else None, int(ldu), _P(stream),
+                                         int(check)))
 
 
 def svd_batched(a, want_u=False, check=True):

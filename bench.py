@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=48, help="bond updates in the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64-side", action="store_true", help="skip the mixed-vs-FP64 side measurement")
     return p.parse_args()
 
 
@@ -323,6 +324,52 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+# ------------------------------------------------- mixed vs FP64 (side) --
+def mixed_vs_fp64(args, local_rank):
+    """The same saturated chi = 256 state (N = 64, built on the FP64 path) is
+    loaded into a mixed and an FP64 state; one layer (with its PtSU step) runs
+    on each; reports device time per gated bond of both paths and the
+    infidelity 1 - F between their results (F from the FP64 contractions)."""
+    import torch
+
+    from paper_2312_02667_gb300 import inputs, ptebd
+
+    n, chi = 64, args.chi
+    dev = torch.device("cuda", local_rank)
+    ref = ptebd.State(n, chi, "fp64", cutoff=1e-12, g=args.g)
+    circuit = inputs.brickwork_circuit(99, n, 12)
+    for parity, _, gates in circuit[:10]:
+        ref.apply_layer(gates, parity)
+    gam, lam = ref.export()
+    out = {}
+    results = {}
+    for prec in ("fp64", "mixed"):
+        st = ptebd.State(n, chi, prec, cutoff=1e-12, g=args.g)
+        st.load(gam, lam)
+        parity, bonds, gates = circuit[10]
+        g_dev = torch.from_numpy(np.ascontiguousarray(gates)).to(dev)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(torch.cuda.current_stream(dev))
+        st.apply_layer(g_dev, parity)
+        e1.record(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[prec] = {"layer_ms": ms, "ms_per_gated_bond_layer": ms / len(bonds)}
+        results[prec] = st
+    a, b = results["fp64"], results["mixed"]
+    ab = a.overlap(b)
+    fid = abs(ab) ** 2 / (a.norm() ** 2 * b.norm() ** 2)
+    out["infidelity_mixed_vs_fp64"] = 1.0 - fid
+    out["speedup_mixed_over_fp64"] = out["fp64"]["layer_ms"] / out["mixed"]["layer_ms"]
+    out["workload"] = (f"N={n}, chi_max={chi}, saturated state (10 FP64 layers), one layer with PtSU g={args.g}; "
+                       "all 32 bonds at theta 512x512; not the headline workload")
+    for st in (ref, a, b):
+        st.close()
+    return out
+
+
 # ------------------------------------------------------------- reference --
 def run_reference(args):
     """The oracle on the host cores, one bounded sample per step."""
@@ -363,6 +410,8 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     result = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_fp64_side:
+        result["mixed_vs_fp64"] = mixed_vs_fp64(args, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, wall, _ = cpu_oracle_sample(args.cpu_sample, args.chi, args.n_sites, args.g)
         result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,

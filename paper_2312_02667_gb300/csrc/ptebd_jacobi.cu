@@ -225,6 +225,10 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     return true;
 }
 
+// Columns are visited in order of decreasing norm, re-sorted at the start of
+// every sweep (de Rijk's ordering idea): it lowers the number of sweeps.
+constexpr int kSortN = 512;
+
 template <typename R, int NW, int RPL>
 __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int cols, int j, unsigned char* smem) {
     using C = cx_t<R>;
@@ -239,6 +243,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     R* in2 = jn2 + 2 * NW;                          // [NW]: |col|^2 of the I block (intra phase)
     int* sh = reinterpret_cast<int*>(in2 + NW);     // [0] rotations, [1] abort
     int* slot_done = sh + 2;  // [2][NW]: rounds completed on each column slot of each stage
+    int* cperm = slot_done + 2 * NW;                                   // [kSortN]: sweep order -> column
+    float* skey = reinterpret_cast<float*>(cperm + kSortN);            // [kSortN]: sort keys
     C* bufJ[2] = {bufJ0, bufJ1};
     int jblocks[2] = {0, 0};  // J blocks processed so far on each stage
     double* nrm2 = A.norms + (size_t)j * ldw;  // squared column norms between blocks (FP64)
@@ -259,7 +265,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         const int nreal = min(NW, cols - c0);
         mbar_expect_tx(&bar[buf], (uint32_t)nreal * col_bytes);
         for (int c = 0; c < nreal; ++c)
-            bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)(c0 + c) * ldw, col_bytes, &bar[buf]);
+            bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)cperm[c0 + c] * ldw, col_bytes, &bar[buf]);
     };
     auto abort_drain = [&](int late_buf, int pending_buf) {
         // Called by all threads after a wait ran out: wait (bounded) once more
@@ -288,12 +294,35 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             if (lane == 0) nrm2[c] = (double)s2;
         }
         __syncthreads();
+        // sweep order: columns by decreasing norm (bitonic sort, ties by index)
+        for (int e = tid; e < kSortN; e += blockDim.x) {
+            skey[e] = e < cols ? (float)nrm2[e] : -1.0f;
+            cperm[e] = e;
+        }
+        __syncthreads();
+        for (int size = 2; size <= kSortN; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int e = tid; e < kSortN; e += blockDim.x) {
+                    const int pe = e ^ stride;
+                    if (pe > e) {
+                        const bool desc = (e & size) == 0;
+                        const float ke = skey[e], kp = skey[pe];
+                        const int ie = cperm[e], ip = cperm[pe];
+                        const bool e_first = (ke > kp) || (ke == kp && ie < ip);
+                        if (desc ? !e_first : e_first) {
+                            skey[e] = kp; skey[pe] = ke; cperm[e] = ip; cperm[pe] = ie;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
         for (int I = 0; I < nb; ++I) {
             // all earlier bulk stores must have landed before plain loads of block I
             if (tid == 0) { bulk_wait_all(); fence_async_global(); }
             __syncthreads();
-            const int my_col = I * NW + warp;
-            const bool mine = my_col < cols;
+            const bool mine = I * NW + warp < cols;
+            const int my_col = mine ? cperm[I * NW + warp] : 0;  // physical column
             C a[RPL];
 #pragma unroll
             for (int q = 0; q < RPL; ++q) {
@@ -361,10 +390,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     const int base = jblocks[cur] * NW;
                     for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
-                        const int gcol = J * NW + jc;
+                        const int lcol = J * NW + jc;
                         if (r > 0) ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
                         if (!ok) break;
-                        if (gcol < cols) {
+                        if (lcol < cols) {
+                            const int gcol = cperm[lcol];  // physical column
                             R be = (r == 0) ? (R)nrm2[gcol] : sn2[jc];
                             if (mine) {
                                 C y[RPL];
@@ -398,7 +428,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         const int c0 = J * NW;
                         const int nreal = min(NW, cols - c0);
                         for (int c = 0; c < nreal; ++c)
-                            bulk_s2g(W + (size_t)(c0 + c) * ldw, buf + (size_t)c * mpad, col_bytes);
+                            bulk_s2g(W + (size_t)cperm[c0 + c] * ldw, buf + (size_t)c * mpad, col_bytes);
                         bulk_commit();
                     }
                     cur = nxt;
@@ -498,7 +528,8 @@ size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (2 + 2 * nw) * sizeof(int);
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (2 + 2 * nw) * sizeof(int) +
+           (size_t)kSortN * (sizeof(int) + sizeof(float));
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

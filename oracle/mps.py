@@ -13,13 +13,20 @@ notes):
 
 * truncation rank k = min(chi_max, #{lambda_a > cutoff * lambda_1}), at least 1;
   everything dropped (by chi_max or by the cutoff) counts in eps_b;
-* eps_b is the discarded FRACTION of the bond's weight, sum_dropped lambda^2 /
-  sum_all lambda^2 (``eps_mode="relative"``, the default).  It equals the
-  paper's eps_i whenever sum lambda^2 = 1 (the normalised canonical state its
-  definition assumes).  ``eps_mode="absolute"`` takes sum_dropped lambda^2
-  literally; off the canonical form the bond weight W = sum lambda^2 drifts
-  from 1, and the absolute reading then multiplies it by (1 - eps)/(1 - W eps)
-  each layer, which runs away (eps_b >= 1) within tens of Haar-random layers;
+* the bond vector is the Schmidt spectrum of the normalised two-site
+  wavefunction, lambda^ = S / |S| (Sec. II B: sum lambda^2 = 1), and the norm
+  stabilisation acts on it (Sec. III C): eps_b = sum_dropped lambda^^2,
+  nu_b = (1 - eps_b)^(-1/2), Lambda_b <- nu_b lambda^_kept
+  (``eps_mode="schmidt"``, the default).  On a normalised canonical state
+  |S| = 1 and this is the paper's update word for word.  Off the canonical
+  form |S| drifts from 1; this reading keeps the wavefunction norm near 1 over
+  many layers in 1D and 2D circuits, which is what the paper reports for its
+  stabilised runs (Sec. IV C, figure of the norms versus depth).  Two other
+  readings are kept for comparison: ``"relative"`` (eps_b = dropped / all S^2,
+  Lambda_b <- nu_b S_kept: the norm then grows exponentially with depth once
+  the bonds truncate, e.g. n* ~ 8e3 after 60 layers at N = 40, chi = 8) and
+  ``"absolute"`` (eps_b = sum_dropped S^2 taken literally, Lambda_b <- nu_b
+  S_kept: eps_b >= 1 within tens of Haar-random layers);
 * Gamma rebuilt by literal division by the neighbouring Lambda (Sec. II C);
 * nu_b is applied to every gated bond (it is exactly 1 when nothing is
   dropped); tSU steps never apply nu;
@@ -55,6 +62,8 @@ __all__ = [
     "from_mps_tensors",
     "truncate_all_bonds",
     "scale_to_unit_norm",
+    "left_environments",
+    "sample",
 ]
 
 
@@ -129,15 +138,18 @@ class BondResult:
 
 
 def update_bond(mps: Vidal, b: int, gate, chi_max: int, cutoff: float,
-                stabilise: bool = True, eps_mode: str = "relative") -> BondResult:
+                stabilise: bool = True, eps_mode: str = "schmidt") -> BondResult:
     """One TEBD procedure on bond b with parallel truncation and norm
     stabilisation, in place.
 
     1. theta = Lambda_{b-1} Gamma_b Lambda_b Gamma_{b+1} Lambda_{b+1}   (Sec. II C)
     2. theta' = U theta (skipped when ``gate is None``: tSU, Sec. III D)
     3. theta' = U S V^dagger (SVD, descending S)                        (Sec. II C)
-    4. keep k values (projector P_b), eps_b = dropped S^2 / all S^2   (Sec. III B, Theorem 1)
-    5. Lambda_b <- nu_b S[:k], nu_b = (1 - eps_b)^(-1/2)                (Sec. III C, stabilised norm)
+    4. keep k values (projector P_b); the Schmidt values of the normalised
+       two-site wavefunction are S / |S|, eps_b = sum of the dropped ones
+       squared                                                       (Sec. II B, III B, Theorem 1)
+    5. Lambda_b <- nu_b S[:k] / |S|, nu_b = (1 - eps_b)^(-1/2)          (Sec. III C, stabilised norm)
+       (tSU, no stabilisation: Lambda_b <- S[:k], the state unchanged)
     6. Gamma_b <- Lambda_{b-1}^{-1} U[:, :k],
        Gamma_{b+1} <- V^dagger[:k, :] Lambda_{b+1}^{-1}                (Sec. II C)
     """
@@ -148,10 +160,12 @@ def update_bond(mps: Vidal, b: int, gate, chi_max: int, cutoff: float,
     mat = theta.reshape(ns * chil, nt * chir)
     u, s, vh = np.linalg.svd(mat, full_matrices=False)
     k = truncation_rank(s, chi_max, cutoff)
-    eps = float(np.sum(s[k:] ** 2))
-    if eps_mode == "relative":
-        eps = eps / float(np.sum(s ** 2))
-    elif eps_mode != "absolute":
+    dropped, total = float(np.sum(s[k:] ** 2)), float(np.sum(s ** 2))
+    if eps_mode in ("schmidt", "relative"):
+        eps = dropped / total
+    elif eps_mode == "absolute":
+        eps = dropped
+    else:
         raise ValueError(eps_mode)
     if stabilise:
         if not eps < 1.0:
@@ -164,7 +178,10 @@ def update_bond(mps: Vidal, b: int, gate, chi_max: int, cutoff: float,
     gr = vh[:k, :].reshape(k, nt, chir).transpose(1, 0, 2) / lr[None, None, :]
     mps.gammas[b] = np.ascontiguousarray(gl)
     mps.gammas[b + 1] = np.ascontiguousarray(gr)
-    mps.lambdas[b] = nu * s[:k].copy()
+    if stabilise and eps_mode == "schmidt":
+        mps.lambdas[b] = nu * (s[:k] / np.sqrt(total))
+    else:
+        mps.lambdas[b] = nu * s[:k].copy()
     return BondResult(b, k, len(s), eps, nu, s)
 
 
@@ -199,7 +216,7 @@ class LayerResult:
 
 
 def apply_bonds(mps: Vidal, bonds, gates, chi_max: int, cutoff: float, g: int = 0,
-                eps_mode: str = "relative") -> LayerResult:
+                eps_mode: str = "schmidt") -> LayerResult:
     """One circuit layer on a set of pairwise non-adjacent bonds (Algorithm 1,
     one pass of the loop over m): the TEBD procedure with compression and
     stabilisation on every listed bond, then g PtSU steps.  The bonds of one
@@ -218,7 +235,7 @@ def apply_bonds(mps: Vidal, bonds, gates, chi_max: int, cutoff: float, g: int = 
 
 
 def apply_layer(mps: Vidal, gates, parity: int, chi_max: int, cutoff: float, g: int = 0,
-                eps_mode: str = "relative") -> LayerResult:
+                eps_mode: str = "schmidt") -> LayerResult:
     """A brickwork layer: gates[j] acts on bond b = parity + 2 j."""
     bonds = list(range(parity, mps.n_sites - 1, 2))
     if len(gates) != len(bonds):
@@ -371,7 +388,55 @@ def truncate_all_bonds(mps: Vidal, chi_keep: int) -> Vidal:
 
 
 def scale_to_unit_norm(mps: Vidal) -> Vidal:
-    """Multiply the state by 1/n by scaling the first site's Gamma."""
+    """Multiply the state by 1/n (n = its norm): every Lambda_b is divided by n
+    and the Gamma of every interior site multiplied by n, a factor
+    n^-(N-1) n^(N-2) = 1/n (N = 1: Gamma_0 / n).  A state that is in canonical
+    form up to a scalar (what PtSU converges to from a state of norm n,
+    Sec. III D) becomes the canonical form of the normalised state: the
+    conditions on A_i = Lambda_{i-1} Gamma_i and B_i = Gamma_i Lambda_i hold at
+    every site afterwards, the end sites included."""
     out = mps.copy()
-    out.gammas[0] = out.gammas[0] / norm(mps)
+    n = norm(mps)
+    if mps.n_sites == 1:
+        out.gammas[0] = out.gammas[0] / n
+        return out
+    out.lambdas = [l / n for l in out.lambdas]
+    for s in range(1, mps.n_sites - 1):
+        out.gammas[s] = out.gammas[s] * n
+    return out
+
+
+# --------------------------------------------------------------------------
+# Sampling (Sec. IV A: bit strings are drawn from the final state)
+# --------------------------------------------------------------------------
+
+def left_environments(mps: Vidal) -> list:
+    """L[s] = the transfer matrix of sites 0..s-1 (L[0] = (1)):
+    L[s+1] = sum_sigma M_s[sigma]^dag L[s] M_s[sigma], M_s = Gamma_s Lambda_s."""
+    envs = [np.ones((1, 1), dtype=np.complex128)]
+    for s in range(mps.n_sites):
+        m = _site_matrix(mps, s)
+        envs.append(_transfer(envs[-1], m, m))
+    return envs
+
+
+def sample(mps: Vidal, uniforms: np.ndarray) -> np.ndarray:
+    """Bit strings drawn from |Psi|^2 / <Psi|Psi> (exact for any MPS), site by
+    site from the right end: with the suffix vector v (chi_s x 1),
+    P(sigma | suffix) is proportional to t^dag L[s] t with t = M_s[sigma] v;
+    sigma = 0 when u < P(0 | suffix).  uniforms: (n_samples, N) numbers in
+    [0, 1), uniforms[k, s] used for site s of sample k."""
+    u = np.asarray(uniforms, dtype=np.float64)
+    envs = left_environments(mps)
+    out = np.zeros(u.shape, dtype=np.int32)
+    for k in range(u.shape[0]):
+        v = np.ones((1, 1), dtype=np.complex128)
+        for s in range(mps.n_sites - 1, -1, -1):
+            m = _site_matrix(mps, s)
+            t = [m[x] @ v for x in range(2)]
+            w = [float((t[x].conj().T @ envs[s] @ t[x]).real[0, 0]) for x in range(2)]
+            p0 = w[0] / (w[0] + w[1])
+            x = 0 if u[k, s] < p0 else 1
+            out[k, s] = x
+            v = t[x] / np.linalg.norm(t[x])
     return out

@@ -176,7 +176,7 @@ def canonical_random(n, chi, seed):
     return oracle.canonicalize(inputs.random_mps_tensors(seed, n, chi))
 
 
-@pytest.mark.parametrize("seed,mode", [(0, "relative"), (1, "relative"), (2, "absolute")])
+@pytest.mark.parametrize("seed,mode", [(0, "schmidt"), (1, "relative"), (2, "absolute"), (3, "schmidt")])
 def test_gate_layer_truncation_against_exact_state(seed, mode):
     # Canonical input, one gate layer, truncated on the gated bonds: Theorem 1
     # (F_2 >= 1 - 2 eps, || Psi - Psi~_T ||^2 <= 2 eps), Lemma 2 (1 - sqrt(2 eps) <= n <= 1)
@@ -262,6 +262,30 @@ def test_ptsu_restores_canonical_form_within_theorem_4(n):
     assert abs(np.linalg.norm(sv.from_vidal(cut)) - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("n", [1, 2, 7])
+def test_scale_to_unit_norm_keeps_canonical_form(n):
+    # A canonical MPS multiplied by c with the factor spread as PtSU leaves it
+    # (every Lambda times c, every interior Gamma divided by c) is not
+    # canonical at the end sites; scaling to unit norm restores the canonical
+    # conditions everywhere and gives back the same normalised vector.
+    mps = canonical_random(n, 8, 11)
+    c = 3.0 ** (1.0 / max(1, n - 1)) if n > 1 else 3.0
+    big = mps.copy()
+    if n == 1:
+        big.gammas[0] = big.gammas[0] * c
+    else:
+        big.lambdas = [l * c for l in big.lambdas]
+        for s in range(1, n - 1):
+            big.gammas[s] = big.gammas[s] / c
+    psi = sv.from_vidal(mps)
+    assert abs(np.linalg.norm(sv.from_vidal(big)) - c) < 1e-12 * c
+    if n > 1:
+        assert oracle.distance_to_canonical(big) > 0.01
+    out = oracle.scale_to_unit_norm(big)
+    assert oracle.distance_to_canonical(out) < 1e-12
+    assert np.abs(sv.from_vidal(out) - psi).max() < 1e-12
+
+
 def test_tsu_on_canonical_state_is_identity_on_lambda():
     mps, _ = run_circuit(9, 7, 64, seed=9)
     before = [l.copy() for l in mps.lambdas]
@@ -287,16 +311,60 @@ def test_norm_decays_without_nu_and_stays_near_one_with_nu():
     assert 0.7 < n_star < 1.5
 
 
-def test_relative_and_absolute_eps_agree_on_canonical_input():
+def test_eps_readings_agree_on_canonical_input():
+    # On a normalised canonical state |S| = 1 on every bond, so the three
+    # readings of eps_b and of the stabilised Lambda_b coincide (Sec. III C).
     n = 10
-    a = canonical_random(n, 16, 5)
-    b = a.copy()
+    base = canonical_random(n, 16, 5)
     parity, bonds, gates = inputs.brickwork_layer(5, n, 0)
-    ra = oracle.apply_layer(a, gates, parity, 6, 1e-12, eps_mode="relative")
-    rb = oracle.apply_layer(b, gates, parity, 6, 1e-12, eps_mode="absolute")
-    assert abs(ra.eps_total - rb.eps_total) < 1e-13
-    for x, y in zip(a.lambdas, b.lambdas):
-        assert np.abs(x - y).max() < 1e-13
+    runs = {}
+    for mode in ("schmidt", "relative", "absolute"):
+        m = base.copy()
+        runs[mode] = (oracle.apply_layer(m, gates, parity, 6, 1e-12, eps_mode=mode), m)
+    ra, a = runs["schmidt"]
+    for mode in ("relative", "absolute"):
+        rb, b = runs[mode]
+        assert abs(ra.eps_total - rb.eps_total) < 1e-13
+        for x, y in zip(a.lambdas, b.lambdas):
+            assert np.abs(x - y).max() < 1e-13
+
+
+def test_schmidt_reading_gives_unit_bond_weight_off_canonical_form():
+    # Closed form of the stabilised update: Lambda_b = nu_b S_kept / |S| with
+    # nu_b^2 = 1 / (1 - eps_b) and eps_b = |S_dropped|^2 / |S|^2, so
+    # sum Lambda_b^2 = 1 on every gated bond whatever the gauge; the relative
+    # reading keeps sum Lambda_b^2 = |S|^2 instead.
+    n = 10
+    ts = [np.asarray(t) for t in inputs.random_mps_tensors(8, n, 8)]
+    raw = oracle.Vidal(ts, [np.linspace(1.5, 0.2, ts[b].shape[2]) for b in range(n - 1)])
+    parity, bonds, gates = inputs.brickwork_layer(8, n, 0)
+    a, b = raw.copy(), raw.copy()
+    ra = oracle.apply_layer(a, gates, parity, 4, 1e-12, eps_mode="schmidt")
+    rb = oracle.apply_layer(b, gates, parity, 4, 1e-12, eps_mode="relative")
+    assert sum(r.eps > 1e-3 for r in ra.bonds) >= 2
+    for r, q in zip(ra.bonds, rb.bonds):
+        total = float(np.sum(r.s_full ** 2))
+        assert abs(total - 1.0) > 1e-2  # off the canonical form
+        assert abs(np.sum(a.lambdas[r.bond] ** 2) - 1.0) < 1e-12
+        assert abs(np.sum(b.lambdas[q.bond] ** 2) - total) < 1e-12 * total
+        assert abs(r.nu ** 2 * (1 - r.eps) - 1.0) < 1e-12
+
+
+def test_stabilised_norm_stays_near_one_over_many_truncating_layers():
+    # Sec. IV C: with the stabilisation the wavefunction norm stays close to 1
+    # with depth (1D and 2D circuits, g = 0).  A 1D brickwork that truncates
+    # on every layer (N = 40, chi = 8, 60 layers): the Schmidt reading stays
+    # near 1; the relative reading, which leaves |S| in Lambda, grows
+    # exponentially and so cannot be the paper's update.
+    n, chi, depth = 40, 8, 60
+    norms = {}
+    for mode in ("schmidt", "relative"):
+        mps = oracle.product_state(n)
+        for parity, bonds, gates in inputs.brickwork_circuit(3, n, depth):
+            oracle.apply_layer(mps, gates, parity, chi, 1e-12, eps_mode=mode)
+        norms[mode] = oracle.norm(mps)
+    assert 0.5 < norms["schmidt"] < 2.0
+    assert norms["relative"] > 100.0
 
 
 # ------------------------------------------------------- planted mistakes ---
@@ -311,7 +379,7 @@ def test_planted_transposed_gate_is_caught(monkeypatch):
 def test_planted_missing_lambda_division_is_caught(monkeypatch):
     real_svd = np.linalg.svd
 
-    def tsu_free_update(mps, b, gate, chi_max, cutoff, stabilise=True, eps_mode="relative"):
+    def tsu_free_update(mps, b, gate, chi_max, cutoff, stabilise=True, eps_mode="schmidt"):
         # same as the oracle but forgets Lambda_{b+1}^{-1} on the right tensor
         theta = oracle.two_site_tensor(mps, b)
         if gate is not None:
@@ -332,7 +400,7 @@ def test_planted_missing_lambda_division_is_caught(monkeypatch):
 def test_planted_missing_nu_breaks_theorem_3(monkeypatch):
     real = oracle.mps.update_bond
 
-    def no_nu(mps, b, gate, chi_max, cutoff, stabilise=True, eps_mode="relative"):
+    def no_nu(mps, b, gate, chi_max, cutoff, stabilise=True, eps_mode="schmidt"):
         return real(mps, b, gate, chi_max, cutoff, False, eps_mode)
 
     monkeypatch.setattr(oracle.mps, "update_bond", no_nu)
@@ -341,3 +409,42 @@ def test_planted_missing_nu_breaks_theorem_3(monkeypatch):
     ry = np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]], dtype=complex)
     oracle.apply_bonds(mps, [0], [CNOT_LR @ np.kron(ry, I2)], 1, 1e-12)
     assert abs(oracle.norm(mps) - 1.0) > 1e-3
+
+
+# ------------------------------------------------------------------ sampling
+
+def test_sampling_follows_statevector_marginals():
+    # the sampler's decisions against conditional probabilities computed
+    # directly from the 2^N amplitudes (a different computation)
+    n = 8
+    mps, psi = run_circuit(n, 6, 64, seed=6)
+    rng = np.random.default_rng(0)
+    u = rng.random((200, n))
+    bits = oracle.sample(mps, u)
+    prob = (np.abs(psi) ** 2).reshape([2] * n)
+    prob = prob / prob.sum()
+    for k in range(u.shape[0]):
+        marg = prob  # sites drawn from the right end
+        for s in range(n - 1, -1, -1):
+            m = marg.reshape(-1, 2).sum(axis=0)
+            p0 = m[0] / m.sum()
+            if abs(u[k, s] - p0) < 1e-9:
+                break  # a tie: both choices are valid
+            x = 0 if u[k, s] < p0 else 1
+            assert bits[k, s] == x
+            marg = marg[..., x]
+
+
+def test_sampling_frequencies_on_a_truncated_state():
+    # a non-canonical (truncated) state: empirical frequencies of the sampler
+    # against |Psi|^2 / <Psi|Psi> (total variation distance)
+    n = 6
+    mps, _ = run_circuit(n, 8, 2, seed=7)
+    psi = sv.from_vidal(mps)
+    p = np.abs(psi) ** 2
+    p /= p.sum()
+    u = np.random.default_rng(1).random((20000, n))
+    bits = oracle.sample(mps, u)
+    idx = bits @ (2 ** np.arange(n - 1, -1, -1))
+    freq = np.bincount(idx, minlength=2 ** n) / len(idx)
+    assert 0.5 * np.abs(freq - p).sum() < 0.03

@@ -69,9 +69,18 @@ enum ptebd_precision {
                          nu, discarded weights, column norms and reductions */
 };
 
+/* Readings of the norm stabilisation (Sec. III C) for a gated bond whose
+ * theta' has singular values S (S_kept: the chi_b kept ones):
+ *   SCHMIDT  (default): the Schmidt spectrum of the normalised two-site
+ *            wavefunction is S / |S| (Sec. II B); eps_b = |S_dropped|^2 / |S|^2,
+ *            nu_b = (1 - eps_b)^(-1/2), Lambda_b <- nu_b S_kept / |S|;
+ *   ABSOLUTE : eps_b = |S_dropped|^2 taken literally, Lambda_b <- nu_b S_kept;
+ *   RELATIVE : eps_b = |S_dropped|^2 / |S|^2, Lambda_b <- nu_b S_kept.
+ * All three coincide on a normalised canonical state (|S| = 1). */
 enum ptebd_eps_mode {
-    PTEBD_EPS_RELATIVE = 0, /* eps_b = dropped S^2 / all S^2 (default) */
-    PTEBD_EPS_ABSOLUTE = 1  /* eps_b = dropped S^2, taken literally */
+    PTEBD_EPS_SCHMIDT = 0,
+    PTEBD_EPS_ABSOLUTE = 1,
+    PTEBD_EPS_RELATIVE = 2
 };
 
 typedef struct ptebd_config {
@@ -197,6 +206,26 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  * out[5..7] = the same three counts (visits, sweeps, SVDs) for the Jacobi runs
  * of the tSU steps alone.  n entries are written (<= 8). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
+
+/* The end of Algorithm 1.  ptebd_canonicalize runs the PtSU steps that
+ * Theorem 4 shows are enough to bring any MPS to canonical form: N/2 steps for
+ * even N, (N-1)/2 for odd N (asynchronous; the state and its norm are
+ * unchanged up to the cutoff).  ptebd_sample draws n_samples bit strings from
+ * |Psi|^2 / <Psi|Psi> exactly for any MPS (canonical or not): the left
+ * environments of every site are contracted in FP64, then the sites are drawn
+ * from the right end, site s of sample k taking 0 when
+ * uniforms[k * N + s] < P(0 | the bits already drawn to its right).
+ * uniforms: host, n_samples * N doubles in [0, 1); bits: host, n_samples * N
+ * int32 (0 or 1).  Scratch: `workspace` (device memory, 256-byte aligned,
+ * owned by the caller, workspace_bytes long) or, when it is NULL, the state's
+ * own workspace; ptebd_sample_workspace_bytes gives the size needed (about
+ * N * chip^2 * 16 bytes, chip = chi_max rounded up to 16 * 2^k), and
+ * ptebd_sample returns PTEBD_ERR_MEMORY when the scratch is smaller.
+ * Synchronous. */
+int ptebd_canonicalize(ptebd_state* st);
+int ptebd_sample_workspace_bytes(const ptebd_state* st, int32_t n_samples, size_t* bytes);
+int ptebd_sample(ptebd_state* st, int32_t n_samples, const double* uniforms, int32_t* bits, void* workspace,
+                 size_t workspace_bytes);
 
 /* Batched serving of independent states (many circuits with uneven N,
  * chi_max and precision): ptebd_batch_create groups n distinct states, which

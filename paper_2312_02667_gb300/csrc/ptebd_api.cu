@@ -136,7 +136,10 @@ int validate_config(const ptebd_config* c, std::string* why) {
     if (c->chi_max < 1) { *why = "chi_max must be >= 1"; return PTEBD_ERR_INVALID; }
     if (c->chi_max > PTEBD_CHI_LIMIT) { *why = "chi_max above PTEBD_CHI_LIMIT"; return PTEBD_ERR_UNSUPPORTED; }
     if (c->precision != PTEBD_FP64 && c->precision != PTEBD_MIXED) { *why = "bad precision"; return PTEBD_ERR_INVALID; }
-    if (c->eps_mode != PTEBD_EPS_RELATIVE && c->eps_mode != PTEBD_EPS_ABSOLUTE) { *why = "bad eps_mode"; return PTEBD_ERR_INVALID; }
+    if (c->eps_mode != PTEBD_EPS_SCHMIDT && c->eps_mode != PTEBD_EPS_ABSOLUTE && c->eps_mode != PTEBD_EPS_RELATIVE) {
+        *why = "bad eps_mode";
+        return PTEBD_ERR_INVALID;
+    }
     if (c->g < 0) { *why = "g must be >= 0"; return PTEBD_ERR_INVALID; }
     if (!(c->cutoff >= 0.0) || !std::isfinite(c->cutoff)) { *why = "cutoff must be finite and >= 0"; return PTEBD_ERR_INVALID; }
     if (std::isnan(c->floor)) { *why = "floor is NaN"; return PTEBD_ERR_INVALID; }
@@ -466,6 +469,32 @@ int contract(ptebd_state* a, ptebd_state* b, int site1, int site2, const double*
     const double sc = std::exp(lg);
     out[0] = e00.x * sc;
     out[1] = e00.y * sc;
+    return PTEBD_OK;
+}
+
+// Left environments E_0..E_{N-1} of `st` (E_0 = (1); E_{s+1} = sum_x M_s[x]^dag E_s M_s[x]),
+// each rescaled by its largest modulus, written to env[s] (chip x chip complex128).
+int left_envs(ptebd_state* st, const std::vector<int32_t>& chi, double2* env, double* logacc) {
+    const int N = st->L.n_sites, ld = st->L.chip;
+    const size_t slice = (size_t)ld * ld;
+    Chain ch = chain_of(st);
+    CUDA_TRY(st, launch_fill_identity(env, 1, 1, ld, st->stream));
+    int rc;
+    for (int s = 0; s + 1 < N; ++s) {
+        const int al = chi[s], ar = chi[s + 1];
+        double2* E = env + (size_t)s * slice;
+        double2* En = env + (size_t)(s + 1) * slice;
+        const double* lam = lam_ptr(st, s);
+        for (int x = 0; x < 2; ++x) {
+            if ((rc = gemm(st, al, ar, al, ONE, E, true, ld, 0, gptr(st, s, x), is64(st), ld, lam, ZERO, ch.mat[2],
+                           ld, nullptr)))
+                return rc;
+            if ((rc = gemm(st, ar, ar, al, ONE, gptr(st, s, x), is64(st), ld, 1, ch.mat[2], true, ld, nullptr,
+                           x == 0 ? ZERO : ONE, En, ld, lam)))
+                return rc;
+        }
+        CUDA_TRY(st, launch_scale_max(En, ar, ar, ld, logacc, st->stream));
+    }
     return PTEBD_OK;
 }
 
@@ -956,6 +985,82 @@ int ptebd_batch_apply_layer(ptebd_batch* b, const double* const* gates, const in
         ptebd_state* st = b->states[i];
         if (cudaStreamWaitEvent(st->stream, b->ev[n], 0) != cudaSuccess) return PTEBD_ERR_CUDA;
         if (key[i] >= 0) ++st->layers;
+    }
+    return PTEBD_OK;
+}
+
+int ptebd_canonicalize(ptebd_state* st) {
+    if (!st) return PTEBD_ERR_INVALID;
+    const int n = st->L.n_sites;
+    return regauge_steps(st, n % 2 == 0 ? n / 2 : (n - 1) / 2);
+}
+
+namespace {
+size_t sample_ws_bytes(int n_sites, int chip, int n_samples) {
+    const int batch = std::max(1, std::min(n_samples, 1024));
+    // N environments, two vector buffers, uniforms and bits of one batch, one log accumulator
+    return align256((size_t)n_sites * chip * chip * sizeof(double2)) +
+           2 * align256((size_t)batch * chip * sizeof(double2)) + align256((size_t)batch * n_sites * sizeof(double)) +
+           align256((size_t)batch * n_sites * sizeof(int32_t)) + 256;
+}
+}  // namespace
+
+int ptebd_sample_workspace_bytes(const ptebd_state* st, int32_t n_samples, size_t* bytes) {
+    if (!st || n_samples < 0 || !bytes) return PTEBD_ERR_INVALID;
+    *bytes = sample_ws_bytes(st->L.n_sites, st->L.chip, n_samples);
+    return PTEBD_OK;
+}
+
+int ptebd_sample(ptebd_state* st, int32_t n_samples, const double* uniforms, int32_t* bits, void* workspace,
+                 size_t workspace_bytes) {
+    if (!st || n_samples < 0 || (n_samples > 0 && (!uniforms || !bits)))
+        return set_err(st, PTEBD_ERR_INVALID, "bad argument");
+    if (n_samples == 0) return PTEBD_OK;
+    if (workspace && ((uintptr_t)workspace & 255))
+        return set_err(st, PTEBD_ERR_INVALID, "the sampling workspace must be 256-byte aligned");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    std::vector<int32_t> chi = host_chi(st, &rc);
+    if (rc) return rc;
+    const int N = st->L.n_sites;
+    const size_t chip = (size_t)st->L.chip, slice = chip * chip;
+    const int batch = std::min(n_samples, 1024);
+    const size_t vec_bytes = (size_t)batch * chip * sizeof(double2);
+    const size_t need = sample_ws_bytes(N, (int)chip, n_samples);
+    char* w = workspace ? static_cast<char*>(workspace) : st->ws;
+    const size_t have = workspace ? workspace_bytes : st->ws_bytes;
+    if (need > have)
+        return set_err(st, PTEBD_ERR_MEMORY, "sampling needs %zu workspace bytes, %zu given", need, have);
+    double2* env = reinterpret_cast<double2*>(w); w += align256((size_t)N * slice * sizeof(double2));
+    double2* va = reinterpret_cast<double2*>(w); w += align256(vec_bytes);
+    double2* vb = reinterpret_cast<double2*>(w); w += align256(vec_bytes);
+    double* du = reinterpret_cast<double*>(w); w += align256((size_t)batch * N * sizeof(double));
+    int32_t* db = reinterpret_cast<int32_t*>(w); w += align256((size_t)batch * N * sizeof(int32_t));
+    double* logacc = reinterpret_cast<double*>(w);
+    CUDA_TRY(st, cudaMemsetAsync(logacc, 0, sizeof(double), st->stream));
+    if ((rc = left_envs(st, chi, env, logacc))) return rc;
+    for (int k0 = 0; k0 < n_samples; k0 += batch) {
+        const int nb = std::min(batch, n_samples - k0);
+        CUDA_TRY(st, cudaMemcpyAsync(du, uniforms + (size_t)k0 * N, (size_t)nb * N * sizeof(double),
+                                     cudaMemcpyHostToDevice, st->stream));
+        const double2* vin = nullptr;  // the right boundary: v = (1)
+        double2* vout = va;
+        for (int s = N - 1; s >= 0; --s) {
+            const int chil = chi[s], chir = chi[s + 1];
+            cudaError_t e;
+            if (is64(st))
+                e = launch_sample_site<double2>(gamma_ptr<double2>(st, s, 0), lam_ptr(st, s), chil, chir, (int)chip,
+                                                env + (size_t)s * slice, vin, vout, du, s, N, db, nb, st->stream);
+            else
+                e = launch_sample_site<float2>(gamma_ptr<float2>(st, s, 0), lam_ptr(st, s), chil, chir, (int)chip,
+                                               env + (size_t)s * slice, vin, vout, du, s, N, db, nb, st->stream);
+            if (e != cudaSuccess) return set_err(st, PTEBD_ERR_CUDA, "sampling launch failed: %s", cudaGetErrorString(e));
+            vin = vout;
+            vout = (vout == va) ? vb : va;
+        }
+        CUDA_TRY(st, cudaMemcpyAsync(bits + (size_t)k0 * N, db, (size_t)nb * N * sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, st->stream));
+        CUDA_TRY(st, cudaStreamSynchronize(st->stream));
     }
     return PTEBD_OK;
 }

@@ -120,7 +120,102 @@ __global__ void k_fill_identity(double2* E, int rows, int cols, int ld) {
     }
 }
 
+// One sampling step at `site` (sites are drawn from the right end), one CTA per
+// sample: t_x = M_site[x] v (x = 0, 1; M = Gamma diag(Lambda_site)),
+// w_x = t_x^dag L t_x with L the left environment of the site, sigma = 0 when
+// u < w_0 / (w_0 + w_1); v <- t_sigma / |t_sigma|.
+// v_in: samples x chip (chir valid entries; nullptr = the unit vector (1) of the
+// right boundary), v_out: samples x chip (chil valid).
+template <typename TG>
+__global__ void __launch_bounds__(256) k_sample_site(const TG* __restrict__ gamma_s, const double* __restrict__ lam,
+                                                     int chil, int chir, int chip, const double2* __restrict__ L,
+                                                     const double2* __restrict__ v_in, double2* __restrict__ v_out,
+                                                     const double* __restrict__ uniforms, int site, int n_sites,
+                                                     int32_t* __restrict__ bits) {
+    __shared__ double2 vs[512];
+    __shared__ double2 ts[2][512];
+    __shared__ double red[3][256];
+    __shared__ int choice;
+    const int k = blockIdx.x, t = threadIdx.x;
+    const size_t slice = (size_t)chip * chip;
+    for (int b = t; b < chir; b += 256) {
+        double2 x = v_in ? v_in[(size_t)k * chip + b] : make_double2(b == 0 ? 1.0 : 0.0, 0.0);
+        x.x *= lam[b]; x.y *= lam[b];
+        vs[b] = x;
+    }
+    __syncthreads();
+    for (int a = t; a < chil; a += 256) {
+        double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
+        for (int b = 0; b < chir; ++b) {
+            const double2 g0 = ld2(gamma_s[(size_t)b * chip + a]);
+            const double2 g1 = ld2(gamma_s[slice + (size_t)b * chip + a]);
+            const double2 x = vs[b];
+            s0.x += g0.x * x.x - g0.y * x.y; s0.y += g0.x * x.y + g0.y * x.x;
+            s1.x += g1.x * x.x - g1.y * x.y; s1.y += g1.x * x.y + g1.y * x.x;
+        }
+        ts[0][a] = s0;
+        ts[1][a] = s1;
+    }
+    __syncthreads();
+    // w_x = sum_a conj(t_x[a]) (L t_x)[a]; |t_x|^2 alongside
+    double w0 = 0.0, w1 = 0.0;
+    for (int a = t; a < chil; a += 256) {
+        double2 u0 = make_double2(0, 0), u1 = make_double2(0, 0);
+        for (int c = 0; c < chil; ++c) {
+            const double2 l = L[(size_t)c * chip + a];
+            const double2 x0 = ts[0][c], x1 = ts[1][c];
+            u0.x += l.x * x0.x - l.y * x0.y; u0.y += l.x * x0.y + l.y * x0.x;
+            u1.x += l.x * x1.x - l.y * x1.y; u1.y += l.x * x1.y + l.y * x1.x;
+        }
+        w0 += ts[0][a].x * u0.x + ts[0][a].y * u0.y;
+        w1 += ts[1][a].x * u1.x + ts[1][a].y * u1.y;
+    }
+    red[0][t] = w0;
+    red[1][t] = w1;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (t < st) { red[0][t] += red[0][t + st]; red[1][t] += red[1][t + st]; }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double p0 = red[0][0] / (red[0][0] + red[1][0]);
+        choice = uniforms[(size_t)k * n_sites + site] < p0 ? 0 : 1;
+        bits[(size_t)k * n_sites + site] = choice;
+    }
+    __syncthreads();
+    const int x = choice;
+    double nn = 0.0;
+    for (int a = t; a < chil; a += 256) nn += ts[x][a].x * ts[x][a].x + ts[x][a].y * ts[x][a].y;
+    red[2][t] = nn;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if (t < st) red[2][t] += red[2][t + st];
+        __syncthreads();
+    }
+    const double inv = red[2][0] > 0.0 ? 1.0 / sqrt(red[2][0]) : 0.0;
+    for (int a = t; a < chil; a += 256) {
+        double2 y = ts[x][a];
+        y.x *= inv; y.y *= inv;
+        v_out[(size_t)k * chip + a] = y;
+    }
+}
+
 }  // namespace
+
+template <typename TG>
+cudaError_t launch_sample_site(const TG* gamma_s, const double* lam, int chil, int chir, int chip, const double2* L,
+                               const double2* v_in, double2* v_out, const double* uniforms, int site, int n_sites,
+                               int32_t* bits, int n_samples, cudaStream_t s) {
+    k_sample_site<TG><<<n_samples, 256, 0, s>>>(gamma_s, lam, chil, chir, chip, L, v_in, v_out, uniforms, site,
+                                                n_sites, bits);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sample_site<float2>(const float2*, const double*, int, int, int, const double2*,
+                                                const double2*, double2*, const double*, int, int, int32_t*, int,
+                                                cudaStream_t);
+template cudaError_t launch_sample_site<double2>(const double2*, const double*, int, int, int, const double2*,
+                                                 const double2*, double2*, const double*, int, int, int32_t*, int,
+                                                 cudaStream_t);
 
 template <typename TA, typename TB>
 cudaError_t launch_zgemm(int m, int n, int k, double2 alpha, const TA* A, int lda, int opA, const TB* B, int ldb,

@@ -107,6 +107,10 @@ cudaError_t launch_zgemm(int m, int n, int k, double2 alpha,
                          const TA* A, int lda, int opA, const TB* B, int ldb,
                          const double* colscale_b, double2 beta, double2* Cm, int ldc,
                          const double* rowscale_c, cudaStream_t s);
+template <typename TG>
+cudaError_t launch_sample_site(const TG* gamma_s, const double* lam, int chil, int chir, int chip, const double2* L,
+                               const double2* v_in, double2* v_out, const double* uniforms, int site, int n_sites,
+                               int32_t* bits, int n_samples, cudaStream_t s);
 cudaError_t launch_scale_max(double2* E, int rows, int cols, int ld, double* log_acc, cudaStream_t s);
 cudaError_t launch_fill_identity(double2* E, int rows, int cols, int ld, cudaStream_t s);
 

@@ -51,15 +51,19 @@ __device__ __forceinline__ int counter_acquire(const int* p) {
     asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
     return v;
 }
-// Bounded spin until *p >= target (or the CTA has aborted).
+// Bounded spin until *p >= target (or the CTA has aborted).  The clock and the
+// abort flag are looked at every 32 polls only, to keep the spin cheap in issue slots.
 __device__ __forceinline__ bool counter_wait_bounded(const int* p, int target, const volatile int* abort_flag) {
+    if (counter_acquire(p) >= target) return true;
     const long long start = clock64();
-    while (counter_acquire(p) < target) {
-        if (clock64() - start > (1ll << 31)) return false;
-        if (*abort_flag) return false;
-        __nanosleep(20);
+    for (unsigned it = 1;; ++it) {
+        __nanosleep(32);
+        if (counter_acquire(p) >= target) return true;
+        if ((it & 31u) == 0u) {
+            if (clock64() - start > (1ll << 31)) return false;
+            if (*abort_flag) return false;
+        }
     }
-    return true;
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -110,13 +114,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // or rounding keeps re-triggering rotations (more sweeps, and every extra
 // rotation adds rounding error to the columns).
 template <typename R> struct Eps;
+// range_e: matrices whose largest entry is not in [2^-range_e, 2^range_e) are
+// rescaled before the sweeps (see the range guard in jacobi_body).
 template <> struct Eps<float> {
     static constexpr double u = 5.9604644775390625e-08;  // 2^-24
     static constexpr double k = 8.0;
+    static constexpr int range_e = 24;
 };
 template <> struct Eps<double> {
     static constexpr double u = 1.1102230246251565e-16;  // 2^-53
     static constexpr double k = 4.0;
+    static constexpr int range_e = 240;
 };
 
 template <typename R>
@@ -124,6 +132,21 @@ __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The binary exponent of a non-negative value, offset so that 0 (no entry) stays
+// below every real exponent: a shared atomicMax over it gives the exponent of the
+// largest entry of a matrix.
+constexpr int kExpOffset = 2048;
+template <typename R> __device__ __forceinline__ int exp_key(R v) {
+    return v > (R)0 ? ilogb((double)v) + kExpOffset : 0;
 }
 
 // Parameters of the rotation that diagonalises [[al, g e], [g conj(e), be]]
@@ -241,8 +264,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);  // [2]: TMA loads of the J stages
     R* jn2 = reinterpret_cast<R*>(bar + 2);        // [2][NW]: tracked |col|^2 of the J stage slots
     R* in2 = jn2 + 2 * NW;                          // [NW]: |col|^2 of the I block (intra phase)
-    int* sh = reinterpret_cast<int*>(in2 + NW);     // [0] rotations, [1] abort
-    int* slot_done = sh + 2;  // [2][NW]: rounds completed on each column slot of each stage
+    int* sh = reinterpret_cast<int*>(in2 + NW);     // [0] rotations, [1] abort, [2] max |entry| (bits)
+    int* slot_done = sh + 3;  // [2][NW]: rounds completed on each column slot of each stage
     int* cperm = slot_done + 2 * NW;                                   // [kSortN]: sweep order -> column
     float* skey = reinterpret_cast<float*>(cperm + kSortN);            // [kSortN]: sort keys
     C* bufJ[2] = {bufJ0, bufJ1};
@@ -279,21 +302,56 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         __syncthreads();
     };
 
-    for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
-        if (tid == 0) { sh[0] = 0; bulk_wait_all(); fence_async_global(); }
-        __syncthreads();
-        // exact squared column norms at the start of every sweep
+    // exact squared column norms (each warp its columns c = warp mod NW); with
+    // want_max, the exponent of the largest |entry| is gathered in sh[2] as well
+    auto norm_pass = [&](bool want_max) {
+        R mx = 0;
         for (int c = warp; c < cols; c += NW) {
             R s0 = 0, s1 = 0;
             for (int r = lane; r < rows; r += 32) {
                 const C v = W[(size_t)c * ldw + r];
                 s0 = fma(v.x, v.x, s0);
                 s1 = fma(v.y, v.y, s1);
+                if (want_max) mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
             }
             const R s2 = warp_sum(s0 + s1);
             if (lane == 0) nrm2[c] = (double)s2;
         }
+        if (want_max) {
+            mx = warp_max(mx);
+            if (lane == 0) atomicMax(&sh[2], exp_key<R>(mx));
+        }
+    };
+    // Range guard.  Squared norms and |a^H b|^2 are formed in R: with entries of
+    // 2^range_e and more they can overflow (and with tiny entries underflow), which
+    // turns a rotation into a plain scaling of the pair.  Such a matrix is scaled by
+    // 2^-e, exactly, so that its largest entry lies in [1, 2), and scaled back after
+    // the sweeps: a power-of-two scaling commutes with every rounding of the sweeps,
+    // so the result equals that of an unbounded exponent range.
+    int scale_e = 0;
+
+    for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
+        if (tid == 0) { sh[0] = 0; bulk_wait_all(); fence_async_global(); }
         __syncthreads();
+        norm_pass(sweep == 0);
+        __syncthreads();
+        if (sweep == 0) {
+            const int ex = sh[2] - kExpOffset;  // 2^ex <= max |entry| < 2^(ex + 1)
+            if (sh[2] > 0 && (ex >= Eps<R>::range_e || ex < -Eps<R>::range_e)) {
+                scale_e = ex;
+                const R f = ldexp((R)1, -scale_e);
+                for (int c = warp; c < cols; c += NW)
+                    for (int r = lane; r < rows; r += 32) {
+                        C v = W[(size_t)c * ldw + r];
+                        v.x *= f; v.y *= f;
+                        W[(size_t)c * ldw + r] = v;
+                    }
+                fence_async_global();  // the sweeps read W through TMA as well
+                __syncwarp();
+                norm_pass(false);
+                __syncthreads();
+            }
+        }
         // sweep order: columns by decreasing norm (bitonic sort, ties by index)
         for (int e = tid; e < kSortN; e += blockDim.x) {
             skey[e] = e < cols ? (float)nrm2[e] : -1.0f;
@@ -469,18 +527,23 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             atomicAdd(&A.work[7], 1ull);
         }
     }
-    // FP64 column norms = singular values
+    // FP64 column norms = singular values; the range guard's scaling is undone
     double* nrm = A.norms + (size_t)j * ldw;
+    const R unscale = ldexp((R)1, scale_e);
     for (int c = warp; c < cols; c += NW) {
         double acc = 0.0;
         for (int r = lane; r < rows; r += 32) {
-            const C v = W[(size_t)c * ldw + r];
+            C v = W[(size_t)c * ldw + r];
             acc = fma((double)v.x, (double)v.x, acc);
             acc = fma((double)v.y, (double)v.y, acc);
+            if (scale_e != 0) {
+                v.x *= unscale; v.y *= unscale;
+                W[(size_t)c * ldw + r] = v;
+            }
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-            const double s = sqrt(acc);
+            const double s = ldexp(sqrt(acc), scale_e);
             if (!isfinite(s)) atomicOr(A.err, DERR_NONFINITE);
             nrm[c] = s;
         }
@@ -506,7 +569,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
         mbar_init(&bar[1], 1);
         mbar_init_fence();
         int* sh = reinterpret_cast<int*>(reinterpret_cast<R*>(bar + 2) + 3 * NW);
-        for (int i = 0; i < 2 + 2 * NW; ++i) sh[i] = 0;  // rotations, abort, slot round counters
+        for (int i = 0; i < 3 + 2 * NW; ++i) sh[i] = 0;  // rotations, abort, max, slot round counters
     }
     fence_async_smem();
     __syncthreads();
@@ -528,7 +591,7 @@ size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (2 + 2 * nw) * sizeof(int) +
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (3 + 2 * nw) * sizeof(int) +
            (size_t)kSortN * (sizeof(int) + sizeof(float));
 }
 

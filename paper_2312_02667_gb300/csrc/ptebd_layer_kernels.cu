@@ -2,7 +2,9 @@
 //   k_theta    : two-site tensor theta = Lambda_{b-1} Gamma_b Lambda_b Gamma_{b+1} Lambda_{b+1}
 //                and theta' = U theta (Sec. II C), batched over the bonds of a layer;
 //   k_truncate : sort the singular values, keep chi' of them (projector P_b, Sec. III B),
-//                eps_b, nu_b = (1 - eps_b)^(-1/2), Lambda_b <- nu_b S (Sec. III C), in FP64;
+//                eps_b, nu_b = (1 - eps_b)^(-1/2), Lambda_b <- nu_b S_kept / |S| (the
+//                Schmidt spectrum of the normalised two-site wavefunction, Sec. II B,
+//                III C; two other readings selectable), in FP64;
 //   k_gamma_*  : Gamma_b <- Lambda_{b-1}^{-1} U and Gamma_{b+1} <- V^dagger Lambda_{b+1}^{-1}
 //                (Sec. II C), one factor straight from the rotated columns, the other
 //                through one complex GEMM with the kept theta';
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
         __syncthreads();
     }
     const double dropped = red[0];
-    double eps = (a.eps_mode == PTEBD_EPS_RELATIVE) ? dropped / total : dropped;
+    double eps = (a.eps_mode == PTEBD_EPS_ABSOLUTE) ? dropped : dropped / total;
     double nu = 1.0;
     if (a.stabilise) {
         if (eps < 1.0) {
@@ -235,8 +237,10 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
             atomicOr(a.err, DERR_EPS);
         }
     }
+    // Lambda_b <- nu S_kept, or nu S_kept / |S| (the Schmidt reading; tSU keeps S)
+    const double lam_scale = (a.stabilise && a.eps_mode == PTEBD_EPS_SCHMIDT) ? nu / sqrt(total) : nu;
     double* lam_b = a.lam + (size_t)(b + 1) * a.chip;
-    for (int q = t; q < a.chip; q += NS) lam_b[q] = (q < k) ? nu * key[q] : 0.0;
+    for (int q = t; q < a.chip; q += NS) lam_b[q] = (q < k) ? lam_scale * key[q] : 0.0;
     if (t < k) {
         a.sig[(size_t)j * a.ldw + t] = key[t];
         a.perm[(size_t)j * a.ldw + t] = idx[t];
@@ -299,11 +303,13 @@ __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
 }
 
 // ------------------------------------------------------------ Gamma, GEMM --
-// The other factor through Z[i, j] = sum_r conj(P[r, i]) Q[r, j]:
-// tall: P = w (columns perm beta), Q = w0 = theta', Z = S^2 V^dag:
-//       Gamma_{b+1}[t](beta, gamma) = Z[beta, (t,gamma)] / (S_beta^2 Lambda_{b+1,gamma})
-// wide: P = w0 = theta'^dag, Q = w (columns perm beta), Z = U S^2:
-//       Gamma_b[s](alpha, beta) = Z[(s,alpha), beta] / (S_beta^2 Lambda_{b-1,alpha})
+// The other factor through Z[i, j] = sum_r conj(P[r, i]) Q[r, j], the rotated
+// columns (U S or V S) divided by S as they are loaded (so that no product of
+// the size of S^2 is formed):
+// tall: P = w (columns perm beta) / S, Q = w0 = theta', Z = S V^dag:
+//       Gamma_{b+1}[t](beta, gamma) = Z[beta, (t,gamma)] / (S_beta Lambda_{b+1,gamma})
+// wide: P = w0 = theta'^dag, Q = w (columns perm beta) / S, Z = U S:
+//       Gamma_b[s](alpha, beta) = Z[(s,alpha), beta] / (S_beta Lambda_{b-1,alpha})
 // grid (ceil(chip/32), ceil(chip/32), 2 count), 256 threads, 2x2 outputs per thread.
 template <typename R>
 __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
@@ -336,18 +342,30 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
     const C* P = tall ? W : W0;
     const C* Q = tall ? W0 : W;
     const int32_t* perm = a.perm + (size_t)j * ldw;
+    const double* sig = a.sig + (size_t)j * ldw;
     __shared__ int pcol[32], qcol[32];
+    __shared__ R pscl[32], qscl[32];
     __shared__ C ps[16][33], qs[16][33];
     if (threadIdx.x < 32) {
         const int row = r0 + threadIdx.x;
         int pc = -1;
-        if (row < rlim) pc = tall ? perm[row] : sg * cl + row;
+        R sc = 1;
+        if (row < rlim) {
+            pc = tall ? perm[row] : sg * cl + row;
+            if (tall) sc = (R)(1.0 / sig[row]);
+        }
         pcol[threadIdx.x] = pc;
+        pscl[threadIdx.x] = sc;
     } else if (threadIdx.x < 64) {
         const int col = c0 + threadIdx.x - 32;
         int qc = -1;
-        if (col < clim) qc = tall ? sg * cr + col : perm[col];
+        R sc = 1;
+        if (col < clim) {
+            qc = tall ? sg * cr + col : perm[col];
+            if (!tall) sc = (R)(1.0 / sig[col]);
+        }
         qcol[threadIdx.x - 32] = qc;
+        qscl[threadIdx.x - 32] = sc;
     }
     __syncthreads();
     C acc[2][2];
@@ -360,8 +378,8 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
             const int kk = e & 15, cc = e >> 4;
             const int r = k0 + kk;
             const int pc = pcol[cc], qc = qcol[cc];
-            ps[kk][cc] = (pc >= 0 && r < rows) ? P[(size_t)pc * ldw + r] : cz<C>();
-            qs[kk][cc] = (qc >= 0 && r < rows) ? Q[(size_t)qc * ldw + r] : cz<C>();
+            ps[kk][cc] = (pc >= 0 && r < rows) ? cscale(P[(size_t)pc * ldw + r], pscl[cc]) : cz<C>();
+            qs[kk][cc] = (qc >= 0 && r < rows) ? cscale(Q[(size_t)qc * ldw + r], qscl[cc]) : cz<C>();
         }
         __syncthreads();
 #pragma unroll 4
@@ -373,7 +391,6 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
         }
         __syncthreads();
     }
-    const double* sig = a.sig + (size_t)j * ldw;
     const double* lnb = a.lam + (size_t)(tall ? b + 2 : b) * chip;  // Lambda_{b+1} or Lambda_{b-1}
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -385,7 +402,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
             if (row < rlim && col < clim) {
                 const double sb = tall ? sig[row] : sig[col];
                 const double ln = tall ? lnb[col] : lnb[row];
-                v = cscale(acc[i][q], (R)(1.0 / (sb * sb * ln)));
+                v = cscale(acc[i][q], (R)(1.0 / (sb * ln)));
             }
             G[(size_t)col * chip + row] = v;
         }
@@ -417,8 +434,9 @@ __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, (R)sc);
 }
 
-// w1 = w0 w diag(1 / sigma_X) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and
-// w = U_X Sigma_X (2 chi_{b-1} x chi_b): w1 = theta^dag U_X = M^dag.
+// w1 = w0 (w diag(1 / sigma_X)) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and
+// w = U_X Sigma_X (2 chi_{b-1} x chi_b): w1 = theta^dag U_X = M^dag (the columns of
+// w are divided by sigma_X as they are loaded; a zero sigma_X gives a zero column).
 // grid (ceil(2 chip / 32), ceil(chip / 32), count), 256 threads.
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
@@ -435,6 +453,13 @@ __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
     C* out = a.w1 + (size_t)j * ldw * ldw;
     const double* sig = a.norms + (size_t)j * ldw;
     __shared__ C as[16][33], bs[16][33];
+    __shared__ R bscl[32];
+    if (threadIdx.x < 32) {
+        const int gc = c0 + threadIdx.x;
+        const double sg = gc < cm ? sig[gc] : 0.0;
+        bscl[threadIdx.x] = sg > 0.0 ? (R)(1.0 / sg) : (R)0;
+    }
+    __syncthreads();
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     C acc[2][2];
 #pragma unroll
@@ -448,7 +473,7 @@ __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
             as[kk][rr] = (gr < rows && gk < kdim) ? A[(size_t)gk * ldw + gr] : cz<C>();
             const int kb = e & 15, cc = e >> 4;
             const int gc = c0 + cc, gkb = k0 + kb;
-            bs[kb][cc] = (gc < cm && gkb < kdim) ? B[(size_t)gc * ldw + gkb] : cz<C>();
+            bs[kb][cc] = (gc < cm && gkb < kdim) ? cscale(B[(size_t)gc * ldw + gkb], bscl[cc]) : cz<C>();
         }
         __syncthreads();
 #pragma unroll 4
@@ -466,8 +491,7 @@ __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
         for (int q = 0; q < 2; ++q) {
             const int gr = r0 + tx + 16 * i, gc = c0 + ty + 16 * q;
             if (gr >= rows || gc >= cm) continue;
-            const double sg = sig[gc];
-            out[(size_t)gc * ldw + gr] = (sg > 0.0) ? cscale(acc[i][q], (R)(1.0 / sg)) : cz<C>();
+            out[(size_t)gc * ldw + gr] = acc[i][q];
         }
 }
 

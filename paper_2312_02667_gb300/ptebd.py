@@ -25,7 +25,7 @@ ERRORS = {
     -9: "PTEBD_ERR_TIMEOUT",
 }
 PTEBD_FP64, PTEBD_MIXED = 0, 1
-PTEBD_EPS_RELATIVE, PTEBD_EPS_ABSOLUTE = 0, 1
+PTEBD_EPS_SCHMIDT, PTEBD_EPS_ABSOLUTE, PTEBD_EPS_RELATIVE = 0, 1, 2
 PTEBD_CHI_LIMIT = 256
 
 # every symbol include/ptebd.h declares
@@ -37,7 +37,7 @@ EXPORTS = (
     "ptebd_bond_stats", "ptebd_svd_sweeps", "ptebd_timing", "ptebd_timing_read",
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
-    "ptebd_svd_batched_noalloc",
+    "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
@@ -96,6 +96,9 @@ _SIGS = {
     "ptebd_batch_apply_layer": (_P, ctypes.POINTER(_D), _I, _I),
     "ptebd_svd_batched_noalloc": (ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P,
                                   ctypes.c_int32, _P, _P, ctypes.c_int32, _P, ctypes.c_int32),
+    "ptebd_canonicalize": (_P,),
+    "ptebd_sample": (_P, ctypes.c_int32, _D, _I, _P, ctypes.c_size_t),
+    "ptebd_sample_workspace_bytes": (_P, ctypes.c_int32, _SZ),
 }
 
 
@@ -133,9 +136,9 @@ def _iptr(a: np.ndarray):
 
 # ---------------------------------------------------------------- C names --
 
-def make_config(n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="relative", floor=-1.0):
+def make_config(n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="schmidt", floor=-1.0):
     prec = {"fp64": PTEBD_FP64, "mixed": PTEBD_MIXED}[precision] if isinstance(precision, str) else int(precision)
-    mode = {"relative": PTEBD_EPS_RELATIVE, "absolute": PTEBD_EPS_ABSOLUTE}[eps_mode] \
+    mode = {"schmidt": PTEBD_EPS_SCHMIDT, "relative": PTEBD_EPS_RELATIVE, "absolute": PTEBD_EPS_ABSOLUTE}[eps_mode] \
         if isinstance(eps_mode, str) else int(eps_mode)
     return ptebd_config(int(n_sites), 2, int(chi_max), prec, int(g), mode, float(cutoff), float(floor))
 
@@ -290,6 +293,26 @@ def ptebd_svd_sweeps(h, n_sites):
     return sw, layers.value
 
 
+def ptebd_canonicalize(h):
+    _check(lib.ptebd_canonicalize(h), h)
+
+
+def ptebd_sample_workspace_bytes(h, n_samples) -> int:
+    out = ctypes.c_size_t()
+    _check(lib.ptebd_sample_workspace_bytes(h, int(n_samples), ctypes.byref(out)), h)
+    return out.value
+
+
+def ptebd_sample(h, uniforms, workspace=None) -> np.ndarray:
+    """Bit strings (n_samples, N) drawn with the given uniforms (n_samples, N);
+    workspace: a CUDA uint8 tensor used as scratch, or None for the state's own."""
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    bits = np.zeros(u.shape, dtype=np.int32)
+    wp, wb = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
+    _check(lib.ptebd_sample(h, u.shape[0], _dptr(u), _iptr(bits), wp, wb), h)
+    return bits
+
+
 def ptebd_timing(h, enable):
     _check(lib.ptebd_timing(h, int(bool(enable))), h)
 
@@ -411,7 +434,7 @@ class Batch:
 class State:
     """One MPS on the current CUDA device, its buffers allocated by torch."""
 
-    def __init__(self, n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="relative",
+    def __init__(self, n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="schmidt",
                  floor=-1.0, workspace_bytes=None, stream=None, device=None):
         import torch
         self.cfg = make_config(n_sites, chi_max, precision, cutoff, g, eps_mode, floor)
@@ -487,6 +510,20 @@ class State:
 
     def svd_sweeps(self):
         return ptebd_svd_sweeps(self.handle, self.n_sites)
+
+    def canonicalize(self):
+        ptebd_canonicalize(self.handle)
+
+    def sample(self, uniforms):
+        """Bit strings drawn with the given uniforms; scratch beyond the
+        state's workspace is allocated for the call."""
+        n = int(np.shape(uniforms)[0])
+        need = ptebd_sample_workspace_bytes(self.handle, n)
+        ws = None
+        if need > self.workspace_bytes:
+            import torch
+            ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return ptebd_sample(self.handle, uniforms, ws)
 
     def timing(self, enable):
         ptebd_timing(self.handle, enable)

@@ -173,6 +173,53 @@ def test_layer_with_ptsu_g1(ptebd, prec):
         assert fidelity(got, ref) >= 1 - FTOL[prec]
 
 
+@pytest.mark.parametrize("prec,k", [("mixed", 24), ("mixed", -24), ("fp64", 24)])
+def test_layer_parity_far_from_unit_norm(ptebd, prec, k):
+    # Every Lambda times 2^k: theta' = U Lambda Gamma Lambda Gamma Lambda grows
+    # by 2^(3k), past what FP32 squared norms and |a^H b|^2 can hold for k = 24
+    # (and below their normal range for k = -24).  The method is homogeneous in
+    # this scale (relative truncation, eps and nu unchanged, every Lambda_b of the
+    # layer scaled alike), so the layer must match the oracle as at unit scale.
+    n, chi = 14, 16
+    mps = oracle.canonicalize(inputs.random_mps_tensors(21, n, chi))
+    mps.lambdas = [l * 2.0 ** k for l in mps.lambdas]
+    st = ptebd.State(n, chi, prec, g=1)
+    for parity, bonds, gates in inputs.brickwork_circuit(22, n, 3):
+        load_into(st, mps)
+        st.apply_layer(gates, parity)
+        oracle.apply_layer(mps, gates, parity, chi, thr(prec), g=1)
+        got = to_oracle(st)
+        for b in range(n - 1):
+            compare_spectra(got.lambdas[b], mps.lambdas[b], TOL[prec], thr(prec), chi)
+        # the fidelity of the states scaled to unit norm (their own norms are
+        # far outside what the FP64 overlap of the helper can square)
+        assert fidelity(oracle.scale_to_unit_norm(got), oracle.scale_to_unit_norm(mps)) >= 1 - FTOL[prec]
+
+
+@pytest.mark.parametrize("mode", ["schmidt", "relative", "absolute"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eps_readings_match_oracle(ptebd, prec, mode):
+    # A Vidal MPS far from the canonical form (random Gammas, graded Lambdas),
+    # where the three readings of the stabilisation differ: one layer each.
+    n, chi = 12, 8
+    ts = [np.asarray(t) for t in inputs.random_mps_tensors(31, n, 8)]
+    # (the absolute reading needs eps_b < 1: smaller Lambdas there)
+    top = 0.6 if mode == "absolute" else 1.5
+    raw = oracle.Vidal(ts, [np.linspace(top, 0.2 * top, ts[b].shape[2]) for b in range(n - 1)])
+    parity, bonds, gates = inputs.brickwork_layer(31, n, 0)
+    st = ptebd.State(n, chi, prec, eps_mode=mode)
+    load_into(st, raw)
+    st.apply_layer(gates, parity)
+    ref = raw.copy()
+    res = oracle.apply_layer(ref, gates, parity, chi, thr(prec), eps_mode=mode)
+    got = to_oracle(st)
+    eps_g, nu_g, _ = st.bond_stats()
+    for r in res.bonds:
+        compare_spectra(got.lambdas[r.bond], ref.lambdas[r.bond], TOL[prec], thr(prec), chi)
+        assert abs(eps_g[r.bond] - r.eps) <= 10 * TOL[prec] * max(r.eps, 1e-3)
+    assert fidelity(got, ref) >= 1 - FTOL[prec]
+
+
 # ---------------------------------------------------------- measurements --
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -332,3 +379,97 @@ def test_device_gates(ptebd):
         b.apply_layer(torch.from_numpy(gates).to("cuda"), parity)
     for s in range(n):
         assert np.array_equal(a.site(s), b.site(s))
+
+
+# ------------------------------------------------------- 2D routed circuits --
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_routed_2d_circuit_against_oracle(ptebd, prec):
+    # a 4x4 lattice, ABCD x 2 with Haar gates, compiled onto the path with
+    # SWAP networks (App. A); every compiled layer through ptebd_apply_bonds
+    from paper_2312_02667_gb300 import circuits2d
+    lx, ly, chi = 4, 4, 16
+    compiled = circuits2d.compile_layers(lx, ly, circuits2d.physical_layers(2, lx, ly, 8))
+    # every compiled layer from the oracle's state (the layer's own parity),
+    # then the whole circuit on the GPU alone against the oracle's trajectory
+    st = ptebd.State(lx * ly, chi, prec)
+    ref = oracle.product_state(lx * ly)
+    for bonds, us in compiled:
+        load_into(st, ref)
+        st.apply_bonds(bonds, us)
+        oracle.apply_bonds(ref, bonds, us, chi, thr(prec))
+        got = to_oracle(st)
+        for b in range(lx * ly - 1):
+            compare_spectra(got.lambdas[b], ref.lambdas[b], TOL[prec], thr(prec), chi)
+        assert fidelity(got, ref) >= 1 - FTOL[prec]
+    st2 = ptebd.State(lx * ly, chi, prec)
+    for bonds, us in compiled:
+        st2.apply_bonds(bonds, us)
+    assert fidelity(to_oracle(st2), ref) >= 1 - len(compiled) * FTOL[prec]
+
+
+def test_routed_32x32_depth8_chi128_sampled(ptebd):
+    # The 2D configuration: 32x32 lattice (1024 qubits) on the path, depth 8
+    # (4 A/B layers + 2 compiled C/D pairs of 3*31 + 2 layers), chi_max = 128,
+    # mixed precision; the last gate layer is checked on 16 sampled bonds
+    # against the oracle's single-bond update of the same inputs.
+    from paper_2312_02667_gb300 import circuits2d
+    lx = ly = 32
+    chi = 128
+    compiled = circuits2d.compile_layers(lx, ly, circuits2d.physical_layers(4, lx, ly, 8))
+    assert len(compiled) == 4 + 2 * 95
+    st = ptebd.State(lx * ly, chi, "mixed")
+    last_gate = max(i for i, (b, u) in enumerate(compiled) if not np.allclose(u[0], circuits2d.SWAP))
+    for bonds, us in compiled[:last_gate]:
+        st.apply_bonds(bonds, us)
+    bonds, us = compiled[last_gate]
+    rng = np.random.default_rng(1)
+    pick = sorted(rng.choice(len(bonds), min(16, len(bonds)), replace=False))
+    n = lx * ly
+    before = {}
+    for j in pick:
+        b = bonds[j]
+        before[j] = (st.lam(b - 1) if b > 0 else np.ones(1), st.site(b), st.lam(b), st.site(b + 1),
+                     st.lam(b + 1) if b + 1 < n - 1 else np.ones(1))
+    st.apply_bonds(bonds, us)
+    eps_g, _, _ = st.bond_stats()
+    for j in pick:
+        b = bonds[j]
+        ll, gb, lb, gb1, lr = before[j]
+        mini = mini_vidal(ll, gb, lb, gb1, lr)
+        r = oracle.update_bond(mini, 1, us[j], chi, thr("mixed"))
+        compare_spectra(st.lam(b), mini.lambdas[1], TOL["mixed"], thr("mixed"), chi)
+        assert abs(eps_g[b] - r.eps) <= 1e-5 * max(r.eps, 1e-3)
+
+
+# ----------------------------------------------- end of Algorithm 1 --------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sampling_matches_oracle(ptebd, prec):
+    # same state, same uniforms: the GPU sampler and the oracle's take the same
+    # decisions (both in FP64 from the same tensors)
+    n, chi = 14, 16
+    st = ptebd.State(n, chi, prec)
+    for parity, bonds, gates in inputs.brickwork_circuit(10, n, 8):
+        st.apply_layer(gates, parity)
+    mps = to_oracle(st)
+    u = np.random.default_rng(3).random((300, n))
+    bits_g = st.sample(u)
+    bits_o = oracle.sample(mps, u)
+    assert np.array_equal(bits_g, bits_o)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_canonicalize_after_truncating_layers(ptebd, prec):
+    n, chi = 12, 8
+    st = ptebd.State(n, chi, prec)
+    for parity, bonds, gates in inputs.brickwork_circuit(12, n, 10):
+        st.apply_layer(gates, parity)
+    before = to_oracle(st)
+    c0 = oracle.distance_to_canonical(oracle.scale_to_unit_norm(before))
+    st.canonicalize()
+    after = to_oracle(st)
+    assert fidelity(before, after) >= 1 - FTOL[prec]
+    c1 = oracle.distance_to_canonical(oracle.scale_to_unit_norm(after))
+    floor = 4 * chi * 8 * np.sqrt(2 * chi) * 2.0 ** -24 if prec == "mixed" else 1e-10
+    assert c0 > 1e-3 and c1 < floor, (c0, c1)

@@ -42,6 +42,28 @@ def test_ginibre_512(env, prec, tol):
         assert np.abs(np.linalg.norm(rows, axis=1) - sig[i]).max() <= tol * 10 * ref[0]
 
 
+@pytest.mark.parametrize("prec,shifts", [("mixed", [-100, -40, 40, 100]), ("fp64", [-700, 600])])
+def test_range_guard_scale_invariance(env, prec, shifts):
+    # sigma(2^k A) = 2^k sigma(A): the kernel forms squared norms and |a^H b|^2 in
+    # its own precision, so without its range guard 2^40 A (complex64) overflows and
+    # rotations turn into plain scalings.  Power-of-two scalings are exact, so the
+    # scaled runs reproduce the unscaled singular values to rounding.
+    torch, ptebd = env
+    rng = np.random.default_rng(7)
+    n = 256
+    a = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2 * n)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    base = torch.from_numpy(a[None]).to(dt).cuda()
+    s0, _ = ptebd.svd_batched(base)
+    s0 = s0.cpu().numpy()[0]
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    for k in shifts:
+        sk, _ = ptebd.svd_batched(base * (2.0 ** k))
+        sk = sk.cpu().numpy()[0] * 2.0 ** -k
+        assert np.all(np.isfinite(sk))
+        assert np.abs(sk - s0).max() <= tol * s0[0], (k, np.abs(sk - s0).max() / s0[0])
+
+
 def test_graded_spectrum_closed_form(env):
     # lambda_a = 10^(-12 a / n): singular values known exactly
     torch, ptebd = env

@@ -80,3 +80,52 @@ def test_uneven_circuits_against_oracle(ptebd):
             compare_spectra(got.lambdas[b], refs[i].lambdas[b], 1e-5, 1e-6, int(chis[i]))
         assert fidelity(got, refs[i]) >= 1 - int(ds[i]) * 1e-6
     batch.close()
+
+
+def test_batched_serving_64_circuits_sampled_bonds(ptebd):
+    # The batched-serving configuration at full size: 64 independent circuits,
+    # N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256}, Haar
+    # gates, mixed precision, one graph launch per layer for all of them.  Each
+    # circuit's last layer is checked on sampled bonds against the oracle's
+    # single-bond update of the same inputs (read back just before that layer).
+    from gpu_helpers import mini_vidal
+    rng = np.random.default_rng(64)
+    k = 64
+    ns = rng.integers(50, 501, k)
+    ds = rng.integers(8, 25, k)
+    chis = rng.choice([32, 64, 128, 256], k)
+    states = [ptebd.State(int(ns[i]), int(chis[i]), "mixed") for i in range(k)]
+    circuits_ = [inputs.brickwork_circuit(300 + i, int(ns[i]), int(ds[i]), circuit=i) for i in range(k)]
+    batch = ptebd.Batch(states)
+    checks = {}
+    for layer in range(int(ds.max())):
+        gl, par = [], []
+        for i in range(k):
+            if layer < ds[i]:
+                parity, bonds, gates = circuits_[i][layer]
+                if layer == ds[i] - 1:  # the last layer of circuit i: snapshot sampled bonds first
+                    n = int(ns[i])
+                    pick = sorted(rng.choice(len(bonds), min(3, len(bonds)), replace=False))
+                    snap = []
+                    for j in pick:
+                        b = int(bonds[j])
+                        st = states[i]
+                        snap.append((b, gates[j], st.lam(b - 1) if b > 0 else np.ones(1), st.site(b), st.lam(b),
+                                     st.site(b + 1), st.lam(b + 1) if b + 1 < n - 1 else np.ones(1)))
+                    checks[i] = snap
+                gl.append(gates)
+                par.append(parity)
+            else:
+                gl.append(None)
+                par.append(-1)
+        batch.apply_layer(gl, par)
+    assert len(checks) == k
+    for i in range(k):
+        chi = int(chis[i])
+        eps_g, _, _ = states[i].bond_stats()
+        for b, u, ll, gb, lb, gb1, lr in checks[i]:
+            mini = mini_vidal(ll, gb, lb, gb1, lr)
+            r = oracle.update_bond(mini, 1, u, chi, 1e-6)
+            compare_spectra(states[i].lam(b), mini.lambdas[1], 1e-5, 1e-6, chi)
+            assert abs(eps_g[b] - r.eps) <= 1e-5 * max(r.eps, 1e-3)
+    batch.close()

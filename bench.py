@@ -174,6 +174,24 @@ def cpu_oracle_sample(n_updates, chi, n_sites, g):
 
 
 # ------------------------------------------------------------------ ours --
+def aggregate(ms_local, work_local, world, device, op_max_seconds=None):
+    """Whole-job numbers of a run over `world` ranks: the time is the maximum
+    over ranks, the work the sum (weak scaling: every rank runs its own
+    replica).  Returns (max ms, summed work, max of op_max_seconds or None).
+    One process per GPU; the collectives go through torch.distributed (NCCL on
+    the GPUs, gloo in the CPU tests)."""
+    if world == 1:
+        return ms_local, work_local, op_max_seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local), float(op_max_seconds or 0.0)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(w)
+    return float(t[0].item()), int(round(float(w[0].item()))), (float(t[1].item()) if op_max_seconds is not None
+                                                               else None)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -227,15 +245,7 @@ def run_ours(args, rank, world, local_rank):
     w1 = st.work_counters()
     st.sync()
     # whole-job aggregation: max time over ranks, sum of work
-    t_max = ms_total
-    gated_all = gated
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-        gg = torch.tensor([float(gated)], device=dev)
-        torch.distributed.all_reduce(gg)
-        gated_all = int(gg.item())
+    t_max, gated_all, _ = aggregate(ms_total, gated, world, dev)
     value = gated_all / (t_max / 1e3)
     ms_per_step = t_max / args.steps
 
@@ -281,15 +291,10 @@ def run_ours(args, rank, world, local_rank):
             h2d += buf.numel() * 8
             layer += 1
         t_e2e = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([t_e2e], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-        e2e = {"value": gated_all / t_e2e if world == 1 else None, "unit": UNIT,
+        _, _, t_e2e = aggregate(0.0, 0, world, dev, op_max_seconds=t_e2e)
+        e2e = {"value": gated_all / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": 16,
                "ms_per_step": 1e3 * t_e2e / args.steps}
-        if world > 1:
-            e2e["value"] = gated_all / t_e2e
 
     result = {
         "metric": METRIC,

@@ -203,7 +203,8 @@ def run_ours(args, rank, world, local_rank):
     n, chi = args.n_sites, args.chi
     st = ptebd.State(n, chi, args.precision, cutoff=1e-12, g=args.g)
     n_layers = args.prefill + args.warmup + args.steps
-    circuit = inputs.brickwork_circuit(7 + rank, n, n_layers + args.steps + 2)
+    diag_layers = 2
+    circuit = inputs.brickwork_circuit(7 + rank, n, n_layers + diag_layers + args.steps + 2)
     dev_gates = [torch.from_numpy(np.ascontiguousarray(g)).to(dev) for (_, _, g) in circuit]
     torch.cuda.synchronize()
 
@@ -226,7 +227,6 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    st.timing(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -240,18 +240,27 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clk = clocks.stop()
     ms_total = ev0.elapsed_time(ev1)
-    kern = st.timing_read()
-    st.timing(False)
     w1 = st.work_counters()
     st.sync()
+    # per-kernel split: a separate pass of `diag_layers` layers with CUDA events
+    # around every launch (which runs the layer on one stream, unchunked)
+    st.timing(True)
+    for _ in range(diag_layers):
+        parity = circuit[layer][0]
+        st.apply_layer(dev_gates[layer], parity)
+        layer += 1
+    st.sync()
+    kern = st.timing_read()
+    st.timing(False)
+    w2 = st.work_counters()
     # whole-job aggregation: max time over ranks, sum of work
     t_max, gated_all, _ = aggregate(ms_total, gated, world, dev)
     value = gated_all / (t_max / 1e3)
     ms_per_step = t_max / args.steps
 
-    # ---- roofline of the dominant kernel (the SVD)
+    # ---- roofline of the dominant kernel (the SVD), from the timed single-stream pass
     svd_ms, svd_launches = kern["svd"]
-    visits = w1[0] - w0[0]
+    visits = w2[0] - w1[0]
     svd_flops = 28.0 * visits
     svd_rate = svd_flops / (svd_ms / 1e3) / 1e12 if svd_ms > 0 else 0.0
     if args.precision == "mixed":
@@ -260,10 +269,11 @@ def run_ours(args, rank, world, local_rank):
     else:
         peak = FP64_TFLOPS_NOMINAL
         peak_note = "FP64 nominal 1.25 TFLOP/s"
-    total_kernel_ms = sum(v[0] for v in kern.values())
-    launches = sum(v[1] for v in kern.values())
-    # gamma = two kernels per recorded launch; everything else one
-    gpu_launches = launches + kern["gamma"][1]
+    # launches in the timed region: per chunk, a gated stage runs 6 kernels (Gamma
+    # is two) and a tSU half-step 9; one more adds the chunks' eps sums
+    n_chunks = min(8, max(1, (n // 2) // 32))
+    per_layer = n_chunks * (6 + 18 * args.g) + (1 if n_chunks > 1 else 0)
+    gpu_launches = args.steps * per_layer
 
     # ---- e2e: host gates (pinned) in, truncation metric out, through the C ABI
     e2e = None
@@ -320,9 +330,13 @@ def run_ours(args, rank, world, local_rank):
             "gated_bonds_per_step": gated / args.steps,
             "tsu_bonds_per_step": args.g * (n - 1),
         },
-        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
-        "kernel_launches_per_step": {k: v[1] / args.steps for k, v in kern.items()},
-        "event_overhead_ms_per_step": (ms_total - total_kernel_ms) / args.steps,
+        "chunk_streams": n_chunks,
+        "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},
+        "kernels_note": ("per-kernel CUDA-event times from a separate pass of the next two layers on one stream "
+                         "(events around every launch serialise the chunks); the timed steps run the chunks "
+                         "concurrently"),
+        "single_stream_ms_per_step": sum(v[0] for v in kern.values()) / diag_layers,
+        "kernel_launches_per_step": {k: v[1] / diag_layers for k, v in kern.items()},
         "svd_sweeps_mean": (w1[3] - w0[3]) / max(1, w1[4] - w0[4]),
         "svd_sweeps_mean_gated": ((w1[3] - w0[3]) - (w1[6] - w0[6])) / max(1, (w1[4] - w0[4]) - (w1[7] - w0[7])),
         "svd_sweeps_mean_tsu": (w1[6] - w0[6]) / max(1, w1[7] - w0[7]),
@@ -342,7 +356,11 @@ def run_ours(args, rank, world, local_rank):
                             "nb(nb-1)/2 times per sweep, and 152 concurrent 2 MB matrices exceed L2",
             "algorithmic": "28 flop per column-pair-row visit x sweeps x n(n-1)/2 x m, counted on the device",
             "peak_source": peak_note,
-            "svd_share_of_step": svd_ms / ms_total if ms_total else None,
+            "svd_share_of_single_stream_step": svd_ms / sum(v[0] for v in kern.values()) if kern else None,
+            "measured_on": "the single-stream pass (the kernel's own launches, CUDA events on its stream)",
+            "achieved_over_timed_steps": 28.0 * (w1[0] - w0[0]) / (ms_total / 1e3) / 1e12 if ms_total > 0 else None,
+            "achieved_over_timed_steps_note": "the same Jacobi flops of the timed steps over their whole wall time "
+                                              "(chunks concurrent, every other kernel included): a lower bound",
         },
         "gpu_launches": int(gpu_launches),
         "clocks": clk,

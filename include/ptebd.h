@@ -138,6 +138,18 @@ int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds,
  * truncation rule) on bonds 0, 2, 4, ... then on bonds 1, 3, 5, ...  */
 int ptebd_regauge(ptebd_state* st, int32_t g);
 
+/* Concurrency of a layer (no counterpart in the paper: a scheduling choice).
+ * The bonds of a layer are split by site range into up to 8 chunks, each run
+ * on a stream of its own; a chunk of the next half-step starts as soon as the
+ * chunks on either side of it are done (a bond touches only its two sites and
+ * the Lambdas next to them), so the tails of the SVD launches overlap with the
+ * rest of the layer.  Results are bit-identical to one stream.  n = 0 (the
+ * default) picks one chunk per 64 bonds of a brickwork layer, at most 8; n = 1
+ * runs everything on the state's stream.  Chunking is also skipped when the
+ * workspace holds fewer slots than the chunks need, while per-kernel timing is
+ * on, and for ptebd_apply_bonds lists that are not in ascending order. */
+int ptebd_set_chunk_streams(ptebd_state* st, int32_t n);
+
 /* Wait for all work of the handle and report latched device errors. */
 int ptebd_sync(ptebd_state* st);
 

@@ -32,8 +32,17 @@ struct ptebd_state {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<int> ev_kind;  // kind of each recorded (start, stop) pair
+    // concurrent bond chunks of a layer: one stream and one event per chunk, and
+    // the fork event (all owned; created on first use)
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> chunk_ev;
+    cudaEvent_t fork_ev = nullptr;
+    int chunk_streams = 0;  // requested number of chunks (0: chosen from N)
     ~ptebd_state() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        for (cudaStream_t x : aux) cudaStreamDestroy(x);
     }
 };
 
@@ -70,6 +79,7 @@ Layout make_layout(const ptebd_config& cfg) {
     L.off_gates = o; o = align256(o + nb * 32 * sizeof(double));
     L.off_bonds = o; o = align256(o + 3 * nb * sizeof(int32_t));
     L.off_scratch = o; o = align256(o + 8 * chip * chip * sizeof(double2) + 8 * sizeof(double));
+    L.off_partials = o; o = align256(o + (size_t)kMaxChunks * 4 * sizeof(double));
     L.state_bytes = o;
     const size_t ldw = (size_t)L.ldw;
     L.slot_w = align256(ldw * ldw * L.elem);
@@ -203,8 +213,56 @@ cudaError_t timed(ptebd_state* st, int kind, F&& f) {
     return e;
 }
 
+// Chunks of a layer.  Bonds are split by site range into k chunks of `width`
+// consecutive bond indices; a stage (the gated bonds, or one half-step of PtSU)
+// has at most `cap` bonds in a chunk (its bonds never share a site).  A bond
+// reads and writes only the tensors of its own two sites and the Lambdas of
+// its neighbours, so a chunk of one stage depends only on chunks c-1, c, c+1
+// of the stage before.
+struct ChunkPlan { int k = 1, width = 0, cap = 0; };
+
+ChunkPlan chunk_plan(const Layout& L, int requested) {
+    ChunkPlan p;
+    int k = requested > 0 ? requested : L.max_bonds / 32;
+    k = std::max(1, std::min(k, std::min(kMaxChunks, std::max(1, (L.n_sites - 1) / 2))));
+    p.k = k;
+    p.width = (L.n_sites - 1 + k - 1) / k;
+    p.cap = (p.width + 1) / 2;
+    return p;
+}
+
+int slots_wanted(const Layout& L) {
+    const ChunkPlan p = chunk_plan(L, 0);
+    return std::max(L.max_bonds, p.k * p.cap);
+}
+
+// One stage of a layer: bonds d_list[0..nb) (ascending when h_list or parity
+// says so), gates for a gated stage.
+struct Stage {
+    const int32_t* d_list;
+    const int32_t* h_list;  // host copy of an explicit list, or nullptr for a parity list
+    int parity;             // parity of the list when h_list == nullptr
+    int nb;
+    const double* d_gates;
+    bool gated;
+};
+
+// Positions [off, off + cnt) of the stage's bonds inside [lo, hi).
+void segment(const Stage& g, int lo, int hi, int* off, int* cnt) {
+    int a, b;
+    if (g.h_list) {
+        a = (int)(std::lower_bound(g.h_list, g.h_list + g.nb, lo) - g.h_list);
+        b = (int)(std::lower_bound(g.h_list, g.h_list + g.nb, hi) - g.h_list);
+    } else {
+        a = std::min(g.nb, std::max(0, (lo - g.parity + 1) / 2));
+        b = std::min(g.nb, std::max(0, (hi - g.parity + 1) / 2));
+    }
+    *off = a;
+    *cnt = std::max(0, b - a);
+}
+
 template <typename R>
-int run_bonds(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_gates, bool gated) {
+LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     const Layout& L = st->L;
     char* m = st->mem;
     WsView ws = ws_view(L, st->ws, st->slots);
@@ -231,53 +289,150 @@ int run_bonds(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_g
     a.totals = at<double>(m, L.off_totals);
     a.err = at<uint32_t>(m, L.off_err);
     a.work = reinterpret_cast<unsigned long long*>(at<double>(m, L.off_totals) + 8);
-    cudaStream_t s = st->stream;
-    for (int c0 = 0; c0 < nb; c0 += st->slots) {
-        a.count = std::min(st->slots, nb - c0);
-        a.bonds = d_bonds + c0;
-        a.gates = gated ? d_gates + (size_t)c0 * 32 : nullptr;
-        CUDA_TRY(st, timed(st, PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
-        if (gated) {
-            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
-        } else {
-            // tSU: SVD of theta = X Y through its rank-chi_b factors
-            LayerArgs<R> x = a;
-            x.pass = 1;
-            LayerArgs<R> y = a;
-            y.w = a.w1;
-            CUDA_TRY(st, timed(st, PTEBD_K_FACTOR, [&] { return launch_xform<R>(x, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(x, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_FACTOR, [&] { return launch_proj<R>(x, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_SVD, [&] { return launch_jacobi<R>(y, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(y, s); }));
-            CUDA_TRY(st, timed(st, PTEBD_K_GAMMA, [&] { return launch_gamma<R>(y, s); }));
-        }
-        CUDA_TRY(st, timed(st, PTEBD_K_REDUCE, [&] {
-                     return launch_reduce_layer(a.slot_eps, a.slot_lognu, a.count, gated ? 1 : 0, a.totals, s);
-                 }));
+    return a;
+}
+
+// The workspace slots [base, base + count) of `a`.
+template <typename R>
+void at_slots(LayerArgs<R>& a, const Layout& L, int base) {
+    const size_t ldw = (size_t)L.ldw, b = (size_t)base;
+    const size_t per_w = L.slot_w / sizeof(cx_t<R>);
+    a.w += b * per_w; a.w0 += b * per_w; a.w1 += b * per_w;
+    a.norms += b * ldw; a.sig += b * ldw; a.perm += b * ldw; a.dims += b * 8;
+    a.slot_eps += b; a.slot_lognu += b; a.slot_sweeps += b;
+}
+
+// The kernel chain of one stage on a.count bonds (slots and bonds already set),
+// on stream s; `wrap(kind, launch)` brackets each launch (timing or not).
+template <typename R, typename W>
+int launch_chain(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&& wrap) {
+    if (gated) {
+        CUDA_TRY(st, wrap(PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
+    } else {
+        // tSU: SVD of theta = X Y through its rank-chi_b factors
+        LayerArgs<R> x = a;
+        x.pass = 1;
+        LayerArgs<R> y = a;
+        y.w = a.w1;
+        CUDA_TRY(st, wrap(PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_xform<R>(x, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(x, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_proj<R>(x, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(y, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(y, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_GAMMA, [&] { return launch_gamma<R>(y, s); }));
+    }
+    CUDA_TRY(st, wrap(PTEBD_K_REDUCE, [&] {
+                 return launch_reduce_layer(a.slot_eps, a.slot_lognu, a.count, gated ? 1 : 0, a.totals, s);
+             }));
+    return PTEBD_OK;
+}
+
+// One stage on the state's stream, in pieces of at most `slots` bonds.
+template <typename R>
+int run_stage_serial(ptebd_state* st, const Stage& g) {
+    auto wrap = [&](int kind, auto&& f) { return timed(st, kind, f); };
+    for (int c0 = 0; c0 < g.nb; c0 += st->slots) {
+        LayerArgs<R> a = stage_args<R>(st, g.gated);
+        a.count = std::min(st->slots, g.nb - c0);
+        a.bonds = g.d_list + c0;
+        a.gates = g.gated ? g.d_gates + (size_t)c0 * 32 : nullptr;
+        int rc = launch_chain<R>(st, a, g.gated, st->stream, wrap);
+        if (rc) return rc;
     }
     return PTEBD_OK;
 }
 
-int run(ptebd_state* st, const int32_t* d_bonds, int nb, const double* d_gates, bool gated) {
-    if (nb <= 0) return PTEBD_OK;
-    return st->cfg.precision == PTEBD_FP64 ? run_bonds<double>(st, d_bonds, nb, d_gates, gated)
-                                           : run_bonds<float>(st, d_bonds, nb, d_gates, gated);
+int ensure_chunk_streams(ptebd_state* st, int k) {
+    while ((int)st->aux.size() < k) {
+        cudaStream_t x;
+        CUDA_TRY(st, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        st->aux.push_back(x);
+        cudaEvent_t e;
+        CUDA_TRY(st, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        st->chunk_ev.push_back(e);
+    }
+    if (!st->fork_ev) CUDA_TRY(st, cudaEventCreateWithFlags(&st->fork_ev, cudaEventDisableTiming));
+    return PTEBD_OK;
 }
 
-int regauge_steps(ptebd_state* st, int g) {
+// All stages of a call, each split into chunks on concurrent streams.  The
+// state's stream forks into the chunk streams and joins them again at the end;
+// chunk c of a stage waits for the events of chunks c-1 and c+1 of the stages
+// before (its own earlier work is ahead of it on its stream).  Every bond runs
+// the same kernels on the same data as on one stream, so the state is
+// bit-identical; the per-chunk eps and ln nu sums go to per-chunk partials that
+// one kernel adds in chunk order.
+template <typename R>
+int run_stages_chunked(ptebd_state* st, const std::vector<Stage>& stages, const ChunkPlan& p) {
+    int rc = ensure_chunk_streams(st, p.k);
+    if (rc) return rc;
+    const Layout& L = st->L;
+    double* part = at<double>(st->mem, L.off_partials);
+    CUDA_TRY(st, cudaMemsetAsync(part, 0, (size_t)kMaxChunks * 4 * sizeof(double), st->stream));
+    CUDA_TRY(st, cudaEventRecord(st->fork_ev, st->stream));
+    for (int c = 0; c < p.k; ++c) CUDA_TRY(st, cudaStreamWaitEvent(st->aux[c], st->fork_ev, 0));
+    auto wrap = [](int, auto&& f) { return f(); };
+    bool recorded[kMaxChunks] = {};
+    for (const Stage& g : stages) {
+        int off[kMaxChunks], cnt[kMaxChunks];
+        for (int c = 0; c < p.k; ++c) segment(g, c * p.width, (c + 1) * p.width, &off[c], &cnt[c]);
+        // first every wait on the neighbours' previous work, then the launches
+        for (int c = 0; c < p.k; ++c) {
+            if (!cnt[c]) continue;
+            for (int nb : {c - 1, c + 1})
+                if (nb >= 0 && nb < p.k && recorded[nb])
+                    CUDA_TRY(st, cudaStreamWaitEvent(st->aux[c], st->chunk_ev[nb], 0));
+        }
+        for (int c = 0; c < p.k; ++c) {
+            if (!cnt[c]) continue;
+            if (cnt[c] > p.cap) return set_err(st, PTEBD_ERR_INVALID, "chunk %d holds %d bonds", c, cnt[c]);
+            LayerArgs<R> a = stage_args<R>(st, g.gated);
+            at_slots(a, L, c * p.cap);
+            a.count = cnt[c];
+            a.bonds = g.d_list + off[c];
+            a.gates = g.gated ? g.d_gates + (size_t)off[c] * 32 : nullptr;
+            a.totals = part + 4 * c;
+            rc = launch_chain<R>(st, a, g.gated, st->aux[c], wrap);
+            if (rc) return rc;
+            CUDA_TRY(st, cudaEventRecord(st->chunk_ev[c], st->aux[c]));
+            recorded[c] = true;
+        }
+    }
+    for (int c = 0; c < p.k; ++c)
+        if (recorded[c]) CUDA_TRY(st, cudaStreamWaitEvent(st->stream, st->chunk_ev[c], 0));
+    CUDA_TRY(st, launch_add_partials(part, p.k, at<double>(st->mem, L.off_totals), st->stream));
+    return PTEBD_OK;
+}
+
+// A gated stage (or none) followed by g PtSU steps.
+int run_layer(ptebd_state* st, const Stage* gated_stage, int g) {
     const Layout& L = st->L;
     const int32_t* lists = at<int32_t>(st->mem, L.off_bonds);
+    std::vector<Stage> stages;
+    if (gated_stage && gated_stage->nb > 0) stages.push_back(*gated_stage);
     for (int step = 0; step < g; ++step) {
-        int r = run(st, lists, n_parity_bonds(L.n_sites, 0), nullptr, false);
-        if (r) return r;
-        r = run(st, lists + L.max_bonds, n_parity_bonds(L.n_sites, 1), nullptr, false);
-        if (r) return r;
+        stages.push_back(Stage{lists, nullptr, 0, n_parity_bonds(L.n_sites, 0), nullptr, false});
+        stages.push_back(Stage{lists + L.max_bonds, nullptr, 1, n_parity_bonds(L.n_sites, 1), nullptr, false});
+    }
+    if (stages.empty()) return PTEBD_OK;
+    const ChunkPlan p = chunk_plan(L, st->chunk_streams);
+    bool chunked = p.k > 1 && !st->timing && st->slots >= p.k * p.cap;
+    for (const Stage& x : stages)
+        if (x.h_list && !std::is_sorted(x.h_list, x.h_list + x.nb)) chunked = false;
+    const bool f64 = st->cfg.precision == PTEBD_FP64;
+    if (chunked) return f64 ? run_stages_chunked<double>(st, stages, p) : run_stages_chunked<float>(st, stages, p);
+    for (const Stage& x : stages) {
+        int rc = f64 ? run_stage_serial<double>(st, x) : run_stage_serial<float>(st, x);
+        if (rc) return rc;
     }
     return PTEBD_OK;
 }
+
+int regauge_steps(ptebd_state* st, int g) { return run_layer(st, nullptr, g); }
 
 const double* stage_gates(ptebd_state* st, const double* gates, int n, int on_device, int* rc) {
     *rc = PTEBD_OK;
@@ -504,9 +659,8 @@ int layer_launches(ptebd_state* st, int parity) {
     const int nb = n_parity_bonds(st->L.n_sites, parity);
     const int32_t* lists = at<int32_t>(st->mem, st->L.off_bonds);
     const double* dg = at<double>(st->mem, st->L.off_gates);
-    int rc = run(st, lists + (parity ? st->L.max_bonds : 0), nb, dg, true);
-    if (rc) return rc;
-    return regauge_steps(st, st->cfg.g);
+    const Stage gs{lists + (parity ? st->L.max_bonds : 0), nullptr, parity, nb, dg, true};
+    return run_layer(st, &gs, st->cfg.g);
 }
 
 }  // namespace
@@ -538,7 +692,7 @@ int ptebd_required_bytes(const ptebd_config* cfg, size_t* state_bytes, size_t* w
     if (rc) return rc;
     Layout L = make_layout(*cfg);
     if (state_bytes) *state_bytes = L.state_bytes;
-    if (workspace_bytes) *workspace_bytes = ws_bytes_for(L, L.max_bonds);
+    if (workspace_bytes) *workspace_bytes = ws_bytes_for(L, slots_wanted(L));
     if (workspace_min_bytes) *workspace_min_bytes = ws_bytes_for(L, 1);
     return PTEBD_OK;
 }
@@ -555,7 +709,8 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
     if (((uintptr_t)state_mem & 255) || ((uintptr_t)workspace & 255)) return PTEBD_ERR_MEMORY;
     if (state_bytes < L.state_bytes) return PTEBD_ERR_MEMORY;
     int slots = 0;
-    while (slots < L.max_bonds && ws_bytes_for(L, slots + 1) <= workspace_bytes) ++slots;
+    const int most = slots_wanted(L);
+    while (slots < most && ws_bytes_for(L, slots + 1) <= workspace_bytes) ++slots;
     if (slots < 1) return PTEBD_ERR_MEMORY;
     ptebd_state* st = new (std::nothrow) ptebd_state();
     if (!st) return PTEBD_ERR_MEMORY;
@@ -573,12 +728,19 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
         return PTEBD_ERR_CUDA;
     }
     rc = ptebd_reset(st);
+    if (!rc) rc = ensure_chunk_streams(st, chunk_plan(L, 0).k);  // created here, never during a capture
     if (rc) {
         delete st;
         return rc;
     }
     *out = st;
     return PTEBD_OK;
+}
+
+int ptebd_set_chunk_streams(ptebd_state* st, int32_t n) {
+    if (!st || n < 0 || n > kMaxChunks) return set_err(st, PTEBD_ERR_INVALID, "chunk streams must be 0..%d", kMaxChunks);
+    st->chunk_streams = n;
+    return ensure_chunk_streams(st, chunk_plan(st->L, n).k);
 }
 
 int ptebd_destroy(ptebd_state* st) {
@@ -622,10 +784,11 @@ int ptebd_apply_layer(ptebd_state* st, const double* gates, int32_t parity, int3
     const double* dg = stage_gates(st, gates, nb, gates_on_device, &rc);
     if (rc) return rc;
     const int32_t* lists = at<int32_t>(st->mem, st->L.off_bonds);
-    rc = run(st, lists + (parity ? st->L.max_bonds : 0), nb, dg, true);
+    const Stage gs{lists + (parity ? st->L.max_bonds : 0), nullptr, parity, nb, dg, true};
+    rc = run_layer(st, &gs, st->cfg.g);
     if (rc) return rc;
     ++st->layers;
-    return regauge_steps(st, st->cfg.g);
+    return PTEBD_OK;
 }
 
 int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds, const double* gates,
@@ -647,10 +810,11 @@ int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds, co
     int rc;
     const double* dg = stage_gates(st, gates, n_bonds, gates_on_device, &rc);
     if (rc) return rc;
-    rc = run(st, dl, n_bonds, dg, true);
+    const Stage gs{dl, bonds, 0, n_bonds, dg, true};
+    rc = run_layer(st, &gs, st->cfg.g);
     if (rc) return rc;
     ++st->layers;
-    return regauge_steps(st, st->cfg.g);
+    return PTEBD_OK;
 }
 
 int ptebd_regauge(ptebd_state* st, int32_t g) {

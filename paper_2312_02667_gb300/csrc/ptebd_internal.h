@@ -58,7 +58,7 @@ struct Layout {
     // state offsets (bytes)
     size_t off_gamma = 0, off_lam = 0, off_chi = 0, off_bond_eps = 0, off_bond_nu = 0,
            off_bond_rank = 0, off_bond_sweeps = 0, off_totals = 0, off_err = 0,
-           off_gates = 0, off_bonds = 0, off_scratch = 0, state_bytes = 0;
+           off_gates = 0, off_bonds = 0, off_scratch = 0, off_partials = 0, state_bytes = 0;
     // per-slot workspace (bytes)
     size_t slot_w = 0, slot_small = 0, slot_bytes = 0;
 };
@@ -96,6 +96,11 @@ template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s);
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
                                 int gated, double* totals, cudaStream_t s);
+// totals[0..2] += sum over c < k of partials[4 c + 0..2], in the order of c
+cudaError_t launch_add_partials(const double* partials, int k, double* totals, cudaStream_t s);
+
+// A layer may run as up to kMaxChunks bond chunks on concurrent streams.
+constexpr int kMaxChunks = 8;
 template <typename R> cudaError_t jacobi_prepare();   // raises the dynamic smem limit
 size_t jacobi_smem_bytes(int precision, int ldw);
 

@@ -514,6 +514,16 @@ __global__ void __launch_bounds__(256) k_reduce_layer(const double* slot_eps, co
     }
 }
 
+// The per-chunk sums of a layer run on concurrent streams, added in chunk order.
+__global__ void k_add_partials(const double* partials, int k, double* totals) {
+    if (threadIdx.x != 0) return;
+    double e = 0.0, l = 0.0, u = 0.0;
+    for (int c = 0; c < k; ++c) { e += partials[4 * c]; l += partials[4 * c + 1]; u += partials[4 * c + 2]; }
+    totals[0] += e;
+    totals[1] += l;
+    totals[2] += u;
+}
+
 // -------------------------------------------------------------- launchers --
 template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
     const int tiles = (a.chip + 31) / 32;
@@ -550,6 +560,11 @@ template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
                                 int gated, double* totals, cudaStream_t s) {
     k_reduce_layer<<<1, 256, 0, s>>>(slot_eps, slot_lognu, count, gated, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_partials(const double* partials, int k, double* totals, cudaStream_t s) {
+    k_add_partials<<<1, 32, 0, s>>>(partials, k, totals);
     return cudaGetLastError();
 }
 

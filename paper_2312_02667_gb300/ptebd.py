@@ -38,6 +38,7 @@ EXPORTS = (
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
+    "ptebd_set_chunk_streams",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
@@ -99,6 +100,7 @@ _SIGS = {
     "ptebd_canonicalize": (_P,),
     "ptebd_sample": (_P, ctypes.c_int32, _D, _I, _P, ctypes.c_size_t),
     "ptebd_sample_workspace_bytes": (_P, ctypes.c_int32, _SZ),
+    "ptebd_set_chunk_streams": (_P, ctypes.c_int32),
 }
 
 
@@ -311,6 +313,10 @@ def ptebd_sample(h, uniforms, workspace=None) -> np.ndarray:
     wp, wb = (workspace.data_ptr(), workspace.numel()) if workspace is not None else (None, 0)
     _check(lib.ptebd_sample(h, u.shape[0], _dptr(u), _iptr(bits), wp, wb), h)
     return bits
+
+
+def ptebd_set_chunk_streams(h, n):
+    _check(lib.ptebd_set_chunk_streams(h, int(n)), h)
 
 
 def ptebd_timing(h, enable):
@@ -527,6 +533,10 @@ class State:
 
     def timing(self, enable):
         ptebd_timing(self.handle, enable)
+
+    def set_chunk_streams(self, n):
+        """Bond chunks a layer may run concurrently (0: automatic, 1: one stream)."""
+        ptebd_set_chunk_streams(self.handle, n)
 
     def timing_read(self):
         return ptebd_timing_read(self.handle)

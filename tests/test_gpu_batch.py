@@ -129,3 +129,23 @@ def test_batched_serving_64_circuits_sampled_bonds(ptebd):
             compare_spectra(states[i].lam(b), mini.lambdas[1], 1e-5, 1e-6, chi)
             assert abs(eps_g[b] - r.eps) <= 1e-5 * max(r.eps, 1e-3)
     batch.close()
+
+
+def test_batch_with_chunked_states(ptebd):
+    # states large enough to run their layers in concurrent chunks, recorded
+    # into the batch graph, against the same states on one stream each
+    specs = [(256, 16), (130, 8), (200, 12)]
+    grouped = [ptebd.State(n, c, "mixed", g=1) for n, c in specs]
+    solo = [ptebd.State(n, c, "mixed", g=1) for n, c in specs]
+    for s in solo:
+        s.set_chunk_streams(1)
+    circuits_ = [inputs.brickwork_circuit(500 + i, n, 6, circuit=i) for i, (n, _) in enumerate(specs)]
+    batch = ptebd.Batch(grouped)
+    for layer in range(6):
+        batch.apply_layer([circuits_[i][layer][2] for i in range(3)], [circuits_[i][layer][0] for i in range(3)])
+        for i in range(3):
+            solo[i].apply_layer(circuits_[i][layer][2], circuits_[i][layer][0])
+    for i, (n, _) in enumerate(specs):
+        for s in range(n):
+            assert np.array_equal(grouped[i].site(s), solo[i].site(s)), (i, s)
+    batch.close()

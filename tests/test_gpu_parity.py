@@ -473,3 +473,41 @@ def test_canonicalize_after_truncating_layers(ptebd, prec):
     c1 = oracle.distance_to_canonical(oracle.scale_to_unit_norm(after))
     floor = 4 * chi * 8 * np.sqrt(2 * chi) * 2.0 ** -24 if prec == "mixed" else 1e-10
     assert c0 > 1e-3 and c1 < floor, (c0, c1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_chunk_streams_bit_identical(ptebd, prec):
+    # A layer split into bond chunks on concurrent streams (the default for
+    # large N) against the same layers on one stream: every bond runs the same
+    # kernels on the same data, so the states are bit-identical.
+    n, chi = 256, 24
+    conc = ptebd.State(n, chi, prec, g=1)
+    one = ptebd.State(n, chi, prec, g=1)
+    one.set_chunk_streams(1)
+    for parity, bonds, gates in inputs.brickwork_circuit(41, n, 8):
+        conc.apply_layer(gates, parity)
+        one.apply_layer(gates, parity)
+    for s in range(n):
+        assert np.array_equal(conc.site(s), one.site(s)), s
+    for b in range(n - 1):
+        assert np.array_equal(conc.lam(b), one.lam(b)), b
+    ea, la = conc.trunc_error()
+    eb, lb = one.trunc_error()
+    assert abs(ea - eb) <= 1e-12 * max(abs(eb), 1e-300) and abs(la - lb) <= 1e-12 * max(abs(lb), 1e-300)
+
+
+def test_chunk_streams_sparse_bonds_and_odd_counts(ptebd):
+    # explicit ascending bond lists (routed 2D layers) and 3 or 5 chunks
+    from paper_2312_02667_gb300 import circuits2d
+    lx = ly = 12
+    compiled = circuits2d.compile_layers(lx, ly, circuits2d.physical_layers(9, lx, ly, 8))[:40]
+    for k in (3, 5):
+        a = ptebd.State(lx * ly, 16, "mixed", g=1)
+        b = ptebd.State(lx * ly, 16, "mixed", g=1)
+        a.set_chunk_streams(k)
+        b.set_chunk_streams(1)
+        for bonds, us in compiled:
+            a.apply_bonds(bonds, us)
+            b.apply_bonds(bonds, us)
+        for s in range(lx * ly):
+            assert np.array_equal(a.site(s), b.site(s)), (k, s)

@@ -74,6 +74,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-side", action="store_true", help="skip the mixed-vs-FP64 side measurement")
+    p.add_argument("--chunk-streams", type=int, default=0, help="bond chunks per layer (0: the library's choice)")
     return p.parse_args()
 
 
@@ -202,6 +203,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     n, chi = args.n_sites, args.chi
     st = ptebd.State(n, chi, args.precision, cutoff=1e-12, g=args.g)
+    if args.chunk_streams:
+        st.set_chunk_streams(args.chunk_streams)
     n_layers = args.prefill + args.warmup + args.steps
     diag_layers = 2
     circuit = inputs.brickwork_circuit(7 + rank, n, n_layers + diag_layers + args.steps + 2)
@@ -271,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
         peak_note = "FP64 nominal 1.25 TFLOP/s"
     # launches in the timed region: per chunk, a gated stage runs 6 kernels (Gamma
     # is two) and a tSU half-step 9; one more adds the chunks' eps sums
-    n_chunks = min(8, max(1, (n // 2) // 32))
+    n_chunks = args.chunk_streams or min(8, max(1, (n // 2) // 32))
     per_layer = n_chunks * (6 + 18 * args.g) + (1 if n_chunks > 1 else 0)
     gpu_launches = args.steps * per_layer
 

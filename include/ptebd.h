@@ -139,7 +139,7 @@ int ptebd_apply_bonds(ptebd_state* st, const int32_t* bonds, int32_t n_bonds,
 int ptebd_regauge(ptebd_state* st, int32_t g);
 
 /* Concurrency of a layer (no counterpart in the paper: a scheduling choice).
- * The bonds of a layer are split by site range into up to 8 chunks, each run
+ * The bonds of a layer are split by site range into up to 16 chunks, each run
  * on a stream of its own; a chunk of the next half-step starts as soon as the
  * chunks on either side of it are done (a bond touches only its two sites and
  * the Lambdas next to them), so the tails of the SVD launches overlap with the

@@ -223,7 +223,7 @@ struct ChunkPlan { int k = 1, width = 0, cap = 0; };
 
 ChunkPlan chunk_plan(const Layout& L, int requested) {
     ChunkPlan p;
-    int k = requested > 0 ? requested : L.max_bonds / 32;
+    int k = requested > 0 ? requested : std::min(8, L.max_bonds / 32);
     k = std::max(1, std::min(k, std::min(kMaxChunks, std::max(1, (L.n_sites - 1) / 2))));
     p.k = k;
     p.width = (L.n_sites - 1 + k - 1) / k;

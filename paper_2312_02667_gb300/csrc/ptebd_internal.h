@@ -100,7 +100,7 @@ cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu
 cudaError_t launch_add_partials(const double* partials, int k, double* totals, cudaStream_t s);
 
 // A layer may run as up to kMaxChunks bond chunks on concurrent streams.
-constexpr int kMaxChunks = 8;
+constexpr int kMaxChunks = 16;
 template <typename R> cudaError_t jacobi_prepare();   // raises the dynamic smem limit
 size_t jacobi_smem_bytes(int precision, int ldw);
 

@@ -23,6 +23,14 @@ template <typename C> __device__ __forceinline__ void cfma(C& acc, C x, C y) {
     acc.x = fma(x.x, y.x, acc.x); acc.x = fma(-x.y, y.y, acc.x);
     acc.y = fma(x.x, y.y, acc.y); acc.y = fma(x.y, y.x, acc.y);
 }
+// 1 / (a b) in the kernel's precision: FP32 arithmetic on the rounded factors
+// for the complex64 path (the FP64 pipe is a small fraction of the FP32 one and
+// these scalings run once per element), FP64 for the complex128 path.
+template <typename R> __device__ __forceinline__ R inv_prod(double a, double b) { return (R)(1.0 / (a * b)); }
+template <> __device__ __forceinline__ float inv_prod<float>(double a, double b) {
+    return __frcp_rn((float)a * (float)b);
+}
+
 // acc += conj(x) * y
 template <typename C> __device__ __forceinline__ void cfma_cj(C& acc, C x, C y) {
     acc.x = fma(x.x, y.x, acc.x); acc.x = fma(x.y, y.y, acc.x);
@@ -58,13 +66,22 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     __shared__ C xs[2][16][33];
     __shared__ C ys[2][16][33];
     __shared__ C ug[16];
+    // the Lambdas of this tile in the kernel's precision (staged once)
+    __shared__ R sL[32], sR[32], sM[PTEBD_CHI_LIMIT];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t slice = (size_t)chip * chip;
     const C* G0 = a.gamma + (size_t)b * 2 * slice;
     const C* G1 = a.gamma + (size_t)(b + 1) * 2 * slice;
-    const double* lL = a.lam + (size_t)b * chip;
-    const double* lM = a.lam + (size_t)(b + 1) * chip;
-    const double* lR = a.lam + (size_t)(b + 2) * chip;
+    {
+        const double* lL = a.lam + (size_t)b * chip;
+        const double* lM = a.lam + (size_t)(b + 1) * chip;
+        const double* lR = a.lam + (size_t)(b + 2) * chip;
+        const int t = threadIdx.x;
+        if (t < 32) sL[t] = (a0 + t < cl) ? (R)lL[a0 + t] : (R)0;
+        else if (t < 64) sR[t - 32] = (g0 + t - 32 < cr) ? (R)lR[g0 + t - 32] : (R)0;
+        for (int q = t; q < cm; q += 256) sM[q] = (R)lM[q];
+        __syncthreads();
+    }
 
     C acc[2][2][2][2];
 #pragma unroll
@@ -82,7 +99,7 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
             const int alpha = a0 + al, beta = k0 + kk;
             C v = cz<C>();
             if (alpha < cl && beta < cm)
-                v = cscale(G0[s * slice + (size_t)beta * chip + alpha], (R)(lL[alpha] * lM[beta]));
+                v = cscale(G0[s * slice + (size_t)beta * chip + alpha], sL[al] * sM[beta]);
             xs[s][kk][al] = v;
         }
         for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -90,7 +107,7 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
             const int gamma = g0 + gg, beta = k0 + kk;
             C v = cz<C>();
             if (gamma < cr && beta < cm)
-                v = cscale(G1[t * slice + (size_t)gamma * chip + beta], (R)lR[gamma]);
+                v = cscale(G1[t * slice + (size_t)gamma * chip + beta], sR[gg]);
             ys[t][kk][gg] = v;
         }
         __syncthreads();
@@ -287,16 +304,14 @@ __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
         // row = alpha, col = beta
         if (col < k && row < cl) {
             const double* lL = a.lam + (size_t)b * chip;
-            const double sc = 1.0 / (sig[col] * lL[row]);
-            v = cscale(W[(size_t)perm[col] * ldw + (size_t)sg * cl + row], (R)sc);
+            v = cscale(W[(size_t)perm[col] * ldw + (size_t)sg * cl + row], inv_prod<R>(sig[col], lL[row]));
         }
         a.gamma[(size_t)b * 2 * slice + sg * slice + e] = v;
     } else {
         // row = beta, col = gamma
         if (row < k && col < cr) {
             const double* lR = a.lam + (size_t)(b + 2) * chip;
-            const double sc = 1.0 / (sig[row] * lR[col]);
-            v = cscale(cconj(W[(size_t)perm[row] * ldw + (size_t)sg * cr + col]), (R)sc);
+            v = cscale(cconj(W[(size_t)perm[row] * ldw + (size_t)sg * cr + col]), inv_prod<R>(sig[row], lR[col]));
         }
         a.gamma[(size_t)(b + 1) * 2 * slice + sg * slice + e] = v;
     }
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
             if (row < rlim && col < clim) {
                 const double sb = tall ? sig[row] : sig[col];
                 const double ln = tall ? lnb[col] : lnb[row];
-                v = cscale(acc[i][q], (R)(1.0 / (sb * ln)));
+                v = cscale(acc[i][q], inv_prod<R>(sb, ln));
             }
             G[(size_t)col * chip + row] = v;
         }
@@ -430,8 +445,8 @@ __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     const int s = r / cl, alpha = r - s * cl;
     const size_t slice = (size_t)chip * chip;
     const C g = a.gamma[(size_t)b * 2 * slice + s * slice + (size_t)beta * chip + alpha];
-    const double sc = a.lam[(size_t)b * chip + alpha] * a.lam[(size_t)(b + 1) * chip + beta];
-    a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, (R)sc);
+    const R sc = (R)a.lam[(size_t)b * chip + alpha] * (R)a.lam[(size_t)(b + 1) * chip + beta];
+    a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, sc);
 }
 
 // w1 = w0 (w diag(1 / sigma_X)) with w0 = theta^dag (2 chi_{b+1} x 2 chi_{b-1}) and

@@ -150,6 +150,17 @@ int ptebd_regauge(ptebd_state* st, int32_t g);
  * on, and for ptebd_apply_bonds lists that are not in ascending order. */
 int ptebd_set_chunk_streams(ptebd_state* st, int32_t n);
 
+/* Test of the failure detection (no counterpart in the paper).  With enable
+ * != 0, in every later SVD launch one warp of each CTA waits, in its first
+ * hand-off, for a round count that nothing ever writes, under a limit of 2^20
+ * clock cycles instead of 2^31: the wait runs out, the CTA's other warps see
+ * its abort flag and stop, the CTA waits for its own copies in flight, latches
+ * DERR_TIMEOUT and returns, and the next synchronising call reports
+ * PTEBD_ERR_TIMEOUT.  Nothing faults or hangs; the state's tensors are left
+ * half-updated (ptebd_reset or an import restores a usable state).  enable = 0
+ * turns it off. */
+int ptebd_test_wait_timeout(ptebd_state* st, int32_t enable);
+
 /* Wait for all work of the handle and report latched device errors. */
 int ptebd_sync(ptebd_state* st);
 

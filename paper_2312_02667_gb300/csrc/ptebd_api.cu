@@ -38,6 +38,7 @@ struct ptebd_state {
     std::vector<cudaEvent_t> chunk_ev;
     cudaEvent_t fork_ev = nullptr;
     int chunk_streams = 0;  // requested number of chunks (0: chosen from N)
+    int wait_test = 0;      // see ptebd_test_wait_timeout
     ~ptebd_state() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
@@ -282,6 +283,7 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     a.eps_mode = st->cfg.eps_mode;
     a.stabilise = gated ? 1 : 0;
     a.max_sweeps = 40;
+    a.wait_test = st->wait_test;
     a.bond_eps = at<double>(m, L.off_bond_eps);
     a.bond_nu = at<double>(m, L.off_bond_nu);
     a.bond_rank = at<int32_t>(m, L.off_bond_rank);
@@ -734,6 +736,12 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
         return rc;
     }
     *out = st;
+    return PTEBD_OK;
+}
+
+int ptebd_test_wait_timeout(ptebd_state* st, int32_t enable) {
+    if (!st) return PTEBD_ERR_INVALID;
+    st->wait_test = enable ? 1 : 0;
     return PTEBD_OK;
 }
 

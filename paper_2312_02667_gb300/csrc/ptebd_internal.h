@@ -76,6 +76,8 @@ struct LayerArgs {
     int count, chip, ldw, n_sites, chi_max;
     double thr_rel;   // relative threshold max(cutoff, floor)
     int eps_mode, stabilise, max_sweeps;
+    int wait_test;    // test of the bounded waits: one hand-off wait per CTA targets a count nothing
+                      // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
     int mode;         // 0: gated bond; 1: tSU through the rank-chi_b factorisation
     int pass;         // Jacobi: 0 = rows/cols from dims, 1 = the X factor (2 chi_{b-1} x chi_b)
     double* bond_eps; double* bond_nu; int32_t* bond_rank; int32_t* bond_sweeps;

@@ -53,14 +53,15 @@ __device__ __forceinline__ int counter_acquire(const int* p) {
 }
 // Bounded spin until *p >= target (or the CTA has aborted).  The clock and the
 // abort flag are looked at every 32 polls only, to keep the spin cheap in issue slots.
-__device__ __forceinline__ bool counter_wait_bounded(const int* p, int target, const volatile int* abort_flag) {
+__device__ __forceinline__ bool counter_wait_bounded(const int* p, int target, const volatile int* abort_flag,
+                                                     long long limit = 1ll << 31) {
     if (counter_acquire(p) >= target) return true;
     const long long start = clock64();
     for (unsigned it = 1;; ++it) {
         __nanosleep(32);
         if (counter_acquire(p) >= target) return true;
         if ((it & 31u) == 0u) {
-            if (clock64() - start > (1ll << 31)) return false;
+            if (clock64() - start > limit) return false;
             if (*abort_flag) return false;
         }
     }
@@ -251,6 +252,7 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
 // Columns are visited in order of decreasing norm, re-sorted at the start of
 // every sweep (de Rijk's ordering idea): it lowers the number of sweeps.
 constexpr int kSortN = 512;
+constexpr int kShInts = 7;  // shared ints ahead of the slot round counters
 
 template <typename R, int NW, int RPL>
 __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int cols, int j, unsigned char* smem) {
@@ -264,8 +266,10 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     uint64_t* bar = reinterpret_cast<uint64_t*>(bufI + NW * mpad);  // [2]: TMA loads of the J stages
     R* jn2 = reinterpret_cast<R*>(bar + 2);        // [2][NW]: tracked |col|^2 of the J stage slots
     R* in2 = jn2 + 2 * NW;                          // [NW]: |col|^2 of the I block (intra phase)
-    int* sh = reinterpret_cast<int*>(in2 + NW);     // [0] rotations, [1] abort, [2] max |entry| (bits)
-    int* slot_done = sh + 3;  // [2][NW]: rounds completed on each column slot of each stage
+    // [0] rotations, [1] abort, [2] max exponent, [3..4] a load into the stage not yet
+    // waited for by thread 0, [5..6] the barrier phase that load completes
+    int* sh = reinterpret_cast<int*>(in2 + NW);
+    int* slot_done = sh + kShInts;  // [2][NW]: rounds completed on each column slot of each stage
     int* cperm = slot_done + 2 * NW;                                   // [kSortN]: sweep order -> column
     float* skey = reinterpret_cast<float*>(cperm + kSortN);            // [kSortN]: sort keys
     C* bufJ[2] = {bufJ0, bufJ1};
@@ -289,13 +293,15 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         mbar_expect_tx(&bar[buf], (uint32_t)nreal * col_bytes);
         for (int c = 0; c < nreal; ++c)
             bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)cperm[c0 + c] * ldw, col_bytes, &bar[buf]);
+        sh[3 + buf] = 1;
+        sh[5 + buf] = (int)phase[buf];
     };
-    auto abort_drain = [&](int late_buf, int pending_buf) {
+    auto abort_drain = [&]() {
         // Called by all threads after a wait ran out: wait (bounded) once more
-        // for the copies still in flight, drain our bulk stores, latch the error.
+        // for the loads still in flight, drain our bulk stores, latch the error.
         if (tid == 0) {
-            mbar_wait_bounded(&bar[late_buf], phase[late_buf]);
-            if (pending_buf >= 0) mbar_wait_bounded(&bar[pending_buf], phase[pending_buf]);
+            for (int b = 0; b < 2; ++b)
+                if (sh[3 + b]) mbar_wait_bounded(&bar[b], (uint32_t)sh[5 + b]);
             bulk_wait_all();
             atomicOr(A.err, DERR_TIMEOUT);
         }
@@ -442,6 +448,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     // squared norm travels with it (global at round 0, then the stage's
                     // slot, and back to global after the last round).
                     bool ok = mbar_wait_bounded(&bar[cur], phase[cur], &sh[1]);
+                    if (tid == 0 && ok) sh[3 + cur] = 0;
                     C* buf = bufJ[cur];
                     int* done = slot_done + cur * NW;
                     R* sn2 = jn2 + cur * NW;
@@ -449,7 +456,12 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
                         const int lcol = J * NW + jc;
-                        if (r > 0) ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
+                        if (r > 0) {
+                            if (A.wait_test && warp == 0 && r == 1 && sweep == 0 && I == 0 && J == 1)
+                                ok = counter_wait_bounded(&done[jc], 0x7fffffff, &sh[1], 1ll << 20);
+                            else
+                                ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
+                        }
                         if (!ok) break;
                         if (lcol < cols) {
                             const int gcol = cperm[lcol];  // physical column
@@ -479,7 +491,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     fence_async_smem();
                     __syncthreads();
                     if (sh[1]) {
-                        abort_drain(cur, (J + 1 < nb) ? nxt : -1);
+                        abort_drain();
                         return;
                     }
                     if (tid == 0) {
@@ -569,7 +581,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
         mbar_init(&bar[1], 1);
         mbar_init_fence();
         int* sh = reinterpret_cast<int*>(reinterpret_cast<R*>(bar + 2) + 3 * NW);
-        for (int i = 0; i < 3 + 2 * NW; ++i) sh[i] = 0;  // rotations, abort, max, slot round counters
+        for (int i = 0; i < kShInts + 2 * NW; ++i) sh[i] = 0;  // counters, flags, slot round counters
     }
     fence_async_smem();
     __syncthreads();
@@ -591,7 +603,7 @@ size_t jacobi_smem_bytes(int precision, int ldw) {
     const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
-    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (3 + 2 * nw) * sizeof(int) +
+    return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (kShInts + 2 * nw) * sizeof(int) +
            (size_t)kSortN * (sizeof(int) + sizeof(float));
 }
 

@@ -38,7 +38,7 @@ EXPORTS = (
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
-    "ptebd_set_chunk_streams",
+    "ptebd_set_chunk_streams", "ptebd_test_wait_timeout",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
 
@@ -101,6 +101,7 @@ _SIGS = {
     "ptebd_sample": (_P, ctypes.c_int32, _D, _I, _P, ctypes.c_size_t),
     "ptebd_sample_workspace_bytes": (_P, ctypes.c_int32, _SZ),
     "ptebd_set_chunk_streams": (_P, ctypes.c_int32),
+    "ptebd_test_wait_timeout": (_P, ctypes.c_int32),
 }
 
 
@@ -317,6 +318,10 @@ def ptebd_sample(h, uniforms, workspace=None) -> np.ndarray:
 
 def ptebd_set_chunk_streams(h, n):
     _check(lib.ptebd_set_chunk_streams(h, int(n)), h)
+
+
+def ptebd_test_wait_timeout(h, enable):
+    _check(lib.ptebd_test_wait_timeout(h, int(bool(enable))), h)
 
 
 def ptebd_timing(h, enable):

@@ -511,3 +511,33 @@ def test_chunk_streams_sparse_bonds_and_odd_counts(ptebd):
             b.apply_bonds(bonds, us)
         for s in range(lx * ly):
             assert np.array_equal(a.site(s), b.site(s)), (k, s)
+
+
+def test_bounded_wait_runs_out_reports_timeout_and_recovers(ptebd):
+    # Failure detection without a GPU fault: one hand-off wait per CTA waits for
+    # a round count nothing writes, under a short limit; the CTAs abort cleanly,
+    # the next synchronising call reports PTEBD_ERR_TIMEOUT, and after a reset
+    # the same state runs a circuit bit-identically to a fresh one.
+    import time
+    n, chi = 32, 32
+    circ = inputs.brickwork_circuit(61, n, 8)
+    st = ptebd.State(n, chi, "mixed")
+    for parity, bonds, gates in circ[:6]:
+        st.apply_layer(gates, parity)
+    st.sync()
+    ptebd.ptebd_test_wait_timeout(st.handle, 1)
+    t0 = time.time()
+    st.apply_layer(circ[6][2], circ[6][0])
+    with pytest.raises(ptebd.PtebdError) as err:
+        st.sync()
+    assert err.value.code == -9  # PTEBD_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    ptebd.ptebd_test_wait_timeout(st.handle, 0)
+    st.sync()  # the error word was cleared when it was reported
+    st.reset()
+    fresh = ptebd.State(n, chi, "mixed")
+    for parity, bonds, gates in circ:
+        st.apply_layer(gates, parity)
+        fresh.apply_layer(gates, parity)
+    for s in range(n):
+        assert np.array_equal(st.site(s), fresh.site(s)), s

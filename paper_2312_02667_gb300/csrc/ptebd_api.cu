@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ptebd_internal.h"
 
 using namespace ptebd;
@@ -410,8 +412,16 @@ int run_stages_chunked(ptebd_state* st, const std::vector<Stage>& stages, const 
     return PTEBD_OK;
 }
 
+// NVTX range around a host-side call (visible in timeline profilers; a no-op
+// without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 // A gated stage (or none) followed by g PtSU steps.
 int run_layer(ptebd_state* st, const Stage* gated_stage, int g) {
+    NvtxRange range(gated_stage ? (g ? "ptebd layer + PtSU" : "ptebd layer") : "ptebd PtSU");
     const Layout& L = st->L;
     const int32_t* lists = at<int32_t>(st->mem, L.off_bonds);
     std::vector<Stage> stages;

@@ -39,12 +39,13 @@ FP32_LANES_PER_SM = 128
 FP64_TFLOPS_NOMINAL = 1.25
 
 # DRAM bytes (read + write) per k_jacobi launch, from one ncu capture of this
-# workload (dram__bytes_read.sum + dram__bytes_write.sum, the five Jacobi
-# launches of one timed step: 306.8, 38.9, 37.8, 29.0, 28.9 GB; averaged per
-# launch), keyed by the SHA-256 of the kernel source it was taken on.  Any other
-# source reports null: the counters no longer describe the kernel.
+# workload on one stream (--chunk-streams 1, the launches the roofline's
+# `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
+# five Jacobi launches of one step: 307.5, 38.9, 37.9, 29.0, 28.8 GB; averaged
+# per launch), keyed by the SHA-256 of the kernel source it was taken on.  Any
+# other source reports null: the counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "1868c36e174fdb5ab370cc2644b27db01b8de10764939fa4e5f75f7e2e5e7e14": 441.3e9 / 5,
+    "3830a466e7a42cc36f38076430aafe61d8f6d0fad59cfb37cbb2b925c565c153": 442.18e9 / 5,
 }
 
 

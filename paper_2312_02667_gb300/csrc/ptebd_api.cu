@@ -463,6 +463,8 @@ int check_device_errors(ptebd_state* st) {
     if (!err) return PTEBD_OK;
     CUDA_TRY(st, cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st->stream));
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (err & DERR_BADARG)
+        return set_err(st, PTEBD_ERR_INVALID, "a bond or bond dimension out of range reached the device (0x%x)", err);
     if (err & DERR_TIMEOUT) return set_err(st, PTEBD_ERR_TIMEOUT, "a bounded device wait ran out (0x%x)", err);
     if (err & DERR_NONFINITE) return set_err(st, PTEBD_ERR_NUMERIC, "non-finite singular value (0x%x)", err);
     if (err & DERR_ZERO_THETA) return set_err(st, PTEBD_ERR_NUMERIC, "zero two-site tensor (0x%x)", err);

@@ -28,6 +28,7 @@ enum : uint32_t {
     DERR_EPS = 4u,           // eps_b >= 1 in absolute mode: nu undefined
     DERR_NOT_CONVERGED = 8u, // a Jacobi SVD hit its sweep limit
     DERR_TIMEOUT = 16u,      // a bounded wait on an mbarrier ran out
+    DERR_BADARG = 32u,       // a bond or bond dimension out of range reached a kernel (skipped)
 };
 
 // ------------------------------------------------------------- layout ----

@@ -49,6 +49,19 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     const int j = blockIdx.z;
     const int b = a.bonds[j];
     const int chip = a.chip;
+    // device-side argument check: a bond or dimension out of range (a corrupted
+    // list or state) is latched as DERR_BADARG and the bond is skipped: zero
+    // rows and columns make the SVD, truncation and Gamma kernels do nothing
+    if (b < 0 || b > a.n_sites - 2 || a.chi[b] < 1 || a.chi[b] > chip || a.chi[b + 1] < 1 ||
+        a.chi[b + 1] > chip || a.chi[b + 2] < 1 || a.chi[b + 2] > chip) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+            int32_t* d = a.dims + j * 8;
+            for (int q = 0; q < 8; ++q) d[q] = 0;
+            d[D_TALL] = 1;
+            atomicOr(a.err, DERR_BADARG);
+        }
+        return;
+    }
     const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
     // tSU (mode 1) always stores theta^dag: its SVD goes through the factors
     const bool tall = a.mode == 0 && cl >= cr;

@@ -127,3 +127,19 @@ def test_oracle_runs_rqc1d_exactly():
     for parity, bonds, gates in comp:
         oracle.apply_layer(mps, gates, parity, chi_max=64, cutoff=1e-12)
     assert sv.fidelity(sv.from_vidal(mps), run_compiled_1d(comp, n)) > 1 - 1e-12
+
+
+@pytest.mark.parametrize("family", ["haar1d", "rqc1d", "pqc1d", "haar2d", "rqc2d", "pqc2d"])
+def test_run_cli_builds_valid_layers(family):
+    # the command-line runner's circuits: every layer's bonds are in range and
+    # pairwise non-adjacent (a layer of the TEBD procedure)
+    from paper_2312_02667_gb300 import run
+    args = run.main.__globals__["argparse"].Namespace(family=family, n=11 if family != "pqc1d" else 12, lx=3, ly=4,
+                                                      depth=8, seed=2)
+    n, layers = run.build_layers(args)
+    assert layers
+    for bonds, gates in layers:
+        bonds = [int(b) for b in bonds]
+        assert len(bonds) == len(gates)
+        assert all(0 <= b <= n - 2 for b in bonds)
+        assert all(c - a >= 2 for a, c in zip(sorted(bonds), sorted(bonds)[1:]))

@@ -107,3 +107,15 @@ def test_norm_stability_2d(ptebd, name):
     for _, n_star, _ in rows:
         assert 0.5 < n_star < 10.0, rows
     assert rows[-1][2] < 1e-30, rows
+
+
+def test_run_cli_json_lines(ptebd, capsys):
+    from paper_2312_02667_gb300 import run
+    import json
+    run.main(["--family", "rqc1d", "--n", "21", "--depth", "6", "--chi", "8", "--norm-every", "3",
+              "--canonicalize", "--samples", "16"])
+    lines = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert len(lines) == 7
+    assert all("eps_total" in row and row["max_chi"] <= 8 for row in lines[:6])
+    assert "n_star" in lines[2] and "n" in lines[2]
+    assert lines[-1]["layers"] == 6 and len(lines[-1]["samples"]) == 8

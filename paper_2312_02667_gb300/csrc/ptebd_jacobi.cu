@@ -157,6 +157,34 @@ template <typename R> __device__ __forceinline__ int exp_key(R v) {
 // preserving when t^2 is below the unit roundoff (cos itself would round to 1 while
 // sin = t does not, and every such rotation would scale the pair by sqrt(1 + t^2)).
 template <typename R> struct RotParams { R cm1, sr, si, tg; };
+// Packed FP32 pairs (fma.rn.f32x2 and friends, sm_100 and later): two lanes of
+// FP32 arithmetic per instruction on a register pair (lo, hi).
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 
 __device__ __forceinline__ RotParams<float> rot_params(float al, float be, float gr, float gi, float g2) {
     // MUFU reciprocal square roots; cos is refined by one Newton step so that
@@ -199,6 +227,29 @@ __device__ __forceinline__ RotParams<double> rot_params(double al, double be, do
     return p;
 }
 
+
+// complex64 rotation of the pair with packed FP32 arithmetic: the same
+// operations as the scalar form, two components per instruction.
+template <int RPL>
+__device__ __forceinline__ void rotate_packed(float2 (&a)[RPL], float2 (&b)[RPL], const RotParams<float>& p) {
+    const unsigned long long sr2 = pk2(p.sr, p.sr), cm2 = pk2(p.cm1, p.cm1);
+    const unsigned long long msr2 = pk2(-p.sr, -p.sr);
+    const unsigned long long msi_pm = pk2(-p.si, p.si);   // (-si, si)
+#pragma unroll
+    for (int q = 0; q < RPL; ++q) {
+        const unsigned long long A = pk2(a[q].x, a[q].y), B = pk2(b[q].x, b[q].y);
+        const unsigned long long As = pk2(a[q].y, a[q].x), Bs = pk2(b[q].y, b[q].x);
+        // -(sr br + si bi, sr bi - si br)
+        const unsigned long long tneg = fma2(msi_pm, Bs, mul2(msr2, B));
+        const unsigned long long an = add2(A, fma2(cm2, A, tneg));
+        // (sr ar - si ai, sr ai + si ar)
+        const unsigned long long t2 = fma2(msi_pm, As, mul2(sr2, A));
+        const unsigned long long bn = add2(B, fma2(cm2, B, t2));
+        a[q] = upk2(an);
+        b[q] = upk2(bn);
+    }
+}
+
 template <typename R, int RPL>
 __device__ __forceinline__ R col_norm2(const cx_t<R> (&a)[RPL]) {
     R s0 = 0, s1 = 0;
@@ -231,6 +282,9 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     const R g2 = gr * gr + gi * gi;
     if (!(g2 > (tol2 * al) * be)) return false;
     const RotParams<R> p = rot_params(al, be, gr, gi, g2);
+    if constexpr (std::is_same<R, float>::value) {
+        rotate_packed<RPL>(a, b, p);
+    } else {
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
         const R ar = a[q].x, ai = a[q].y, br = b[q].x, bi = b[q].y;
@@ -238,6 +292,7 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
         a[q].y = ai + (p.cm1 * ai - (p.sr * bi - p.si * br));
         b[q].x = br + (p.cm1 * br + (p.sr * ar - p.si * ai));
         b[q].y = bi + (p.cm1 * bi + (p.sr * ai + p.si * ar));
+    }
     }
     // norms from the 2x2 problem; the one that shrinks is recomputed when it
     // lost most of its size (cancellation in the update)

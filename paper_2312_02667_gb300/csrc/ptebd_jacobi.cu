@@ -304,6 +304,82 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     return true;
 }
 
+
+// Rows of a column held by a lane, RPL entries per lane.  complex64 with RPL >= 2:
+// entry q is row 64 (q / 2) + 2 lane + (q & 1), adjacent rows in pairs, moved
+// with 16-byte accesses; otherwise entry q is row 32 q + lane.
+template <typename C, int RPL> struct PairRows {
+    static constexpr bool on = std::is_same<C, float2>::value && RPL >= 2;
+};
+template <typename C, int RPL>
+__device__ __forceinline__ int lane_row(int lane, int q) {
+    return PairRows<C, RPL>::on ? 64 * (q >> 1) + 2 * lane + (q & 1) : 32 * q + lane;
+}
+// v[q] = col[row(q)] for rows < rows (else 0); col 16-byte aligned
+template <typename C, int RPL>
+__device__ __forceinline__ void col_load(C (&v)[RPL], const C* col, int lane, int rows, bool valid) {
+    if constexpr (PairRows<C, RPL>::on) {
+#pragma unroll
+        for (int h = 0; h < RPL / 2; ++h) {
+            const int r = 64 * h + 2 * lane;  // rows is even: a pair is valid as a whole
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid && r < rows) t = *reinterpret_cast<const float4*>(col + r);
+            v[2 * h] = make_float2(t.x, t.y);
+            v[2 * h + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = 32 * q + lane;
+            v[q] = (valid && r < rows) ? col[r] : cmake<C>(0, 0);
+        }
+    }
+}
+template <typename C, int RPL>
+__device__ __forceinline__ void col_store(const C (&v)[RPL], C* col, int lane, int rows) {
+    if constexpr (PairRows<C, RPL>::on) {
+#pragma unroll
+        for (int h = 0; h < RPL / 2; ++h) {
+            const int r = 64 * h + 2 * lane;
+            if (r < rows) *reinterpret_cast<float4*>(col + r) = make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int r = 32 * q + lane;
+            if (r < rows) col[r] = v[q];
+        }
+    }
+}
+// the same for a shared-memory column slot padded with zeros to mpad rows:
+// every row is read and written (rows beyond `rows` stay zero)
+template <typename C, int RPL>
+__device__ __forceinline__ void slot_load(C (&v)[RPL], const C* col, int lane) {
+    if constexpr (PairRows<C, RPL>::on) {
+#pragma unroll
+        for (int h = 0; h < RPL / 2; ++h) {
+            const float4 t = *reinterpret_cast<const float4*>(col + 64 * h + 2 * lane);
+            v[2 * h] = make_float2(t.x, t.y);
+            v[2 * h + 1] = make_float2(t.z, t.w);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) v[q] = col[32 * q + lane];
+    }
+}
+template <typename C, int RPL>
+__device__ __forceinline__ void slot_store(const C (&v)[RPL], C* col, int lane) {
+    if constexpr (PairRows<C, RPL>::on) {
+#pragma unroll
+        for (int h = 0; h < RPL / 2; ++h)
+            *reinterpret_cast<float4*>(col + 64 * h + 2 * lane) =
+                make_float4(v[2 * h].x, v[2 * h].y, v[2 * h + 1].x, v[2 * h + 1].y);
+    } else {
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) col[32 * q + lane] = v[q];
+    }
+}
+
 // Columns are visited in order of decreasing norm, re-sorted at the start of
 // every sweep (de Rijk's ordering idea): it lowers the number of sweeps.
 constexpr int kSortN = 512;
@@ -443,14 +519,9 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             const bool mine = I * NW + warp < cols;
             const int my_col = mine ? cperm[I * NW + warp] : 0;  // physical column
             C a[RPL];
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) {
-                const int r = lane + 32 * q;
-                a[q] = (mine && r < rows) ? W[(size_t)my_col * ldw + r] : cmake<C>(0, 0);
-            }
+            col_load<C, RPL>(a, W + (size_t)my_col * ldw, lane, rows, mine);
             // ---- intra-block pairs of I (round-robin), in shared memory
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) bufI[(size_t)warp * mpad + lane + 32 * q] = a[q];
+            slot_store<C, RPL>(a, bufI + (size_t)warp * mpad, lane);
             if (lane == 0) in2[warp] = mine ? (R)nrm2[my_col] : (R)0;
             __syncthreads();
             for (int r = 0; r < NW - 1; ++r) {
@@ -459,18 +530,12 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     const int p = player(warp), q2 = player(NW - 1 - warp);
                     if (I * NW + p < cols && I * NW + q2 < cols) {
                         C x[RPL], y[RPL];
-#pragma unroll
-                        for (int q = 0; q < RPL; ++q) {
-                            x[q] = bufI[(size_t)p * mpad + lane + 32 * q];
-                            y[q] = bufI[(size_t)q2 * mpad + lane + 32 * q];
-                        }
+                        slot_load<C, RPL>(x, bufI + (size_t)p * mpad, lane);
+                        slot_load<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
                         R nx = in2[p], ny = in2[q2];
                         if (pair_rotate<R, RPL>(x, y, nx, ny, tol2)) {
-#pragma unroll
-                            for (int q = 0; q < RPL; ++q) {
-                                bufI[(size_t)p * mpad + lane + 32 * q] = x[q];
-                                bufI[(size_t)q2 * mpad + lane + 32 * q] = y[q];
-                            }
+                            slot_store<C, RPL>(x, bufI + (size_t)p * mpad, lane);
+                            slot_store<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
                             __syncwarp();
                             if (lane == 0) {
                                 in2[p] = nx;
@@ -482,8 +547,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                 }
                 __syncthreads();
             }
-#pragma unroll
-            for (int q = 0; q < RPL; ++q) a[q] = bufI[(size_t)warp * mpad + lane + 32 * q];
+            slot_load<C, RPL>(a, bufI + (size_t)warp * mpad, lane);
             R al = in2[warp];
 
             // ---- cross pairs with every later block J, streamed by TMA
@@ -523,11 +587,9 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             R be = (r == 0) ? (R)nrm2[gcol] : sn2[jc];
                             if (mine) {
                                 C y[RPL];
-#pragma unroll
-                                for (int q = 0; q < RPL; ++q) y[q] = buf[(size_t)jc * mpad + lane + 32 * q];
+                                slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                 if (pair_rotate<R, RPL>(a, y, al, be, tol2)) {
-#pragma unroll
-                                    for (int q = 0; q < RPL; ++q) buf[(size_t)jc * mpad + lane + 32 * q] = y[q];
+                                    slot_store<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                     if (lane == 0) atomicAdd(&sh[0], 1);
                                 }
                             }
@@ -561,11 +623,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             }
             // write block I back
             if (mine) {
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) {
-                    const int r = lane + 32 * q;
-                    if (r < rows) W[(size_t)my_col * ldw + r] = a[q];
-                }
+                col_store<C, RPL>(a, W + (size_t)my_col * ldw, lane, rows);
                 if (lane == 0) nrm2[my_col] = (double)al;
             }
             fence_async_global();

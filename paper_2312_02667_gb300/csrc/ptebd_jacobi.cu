@@ -405,7 +405,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     float* skey = reinterpret_cast<float*>(cperm + kSortN);            // [kSortN]: sort keys
     C* bufJ[2] = {bufJ0, bufJ1};
     int jblocks[2] = {0, 0};  // J blocks processed so far on each stage
-    double* nrm2 = A.norms + (size_t)j * ldw;  // squared column norms between blocks (FP64)
+    // squared column norms between blocks (FP64), a table in shared memory
+    double* nrm2 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(skey + kSortN) + 7) & ~uintptr_t(7));
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
     const R tol2 = tol * tol;
@@ -564,8 +565,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     // slot's round counter (release / acquire), so a warp only waits for
                     // its one predecessor; the counters only grow, so a waiter can never
                     // mistake an older round for the one it needs.  The column's tracked
-                    // squared norm travels with it (global at round 0, then the stage's
-                    // slot, and back to global after the last round).
+                    // squared norm travels with it (the CTA's norm table at round 0, then the
+                    // stage's slot, and back to the table after the last round).
                     bool ok = mbar_wait_bounded(&bar[cur], phase[cur], &sh[1]);
                     if (tid == 0 && ok) sh[3 + cur] = 0;
                     C* buf = bufJ[cur];
@@ -717,7 +718,7 @@ size_t jacobi_smem_bytes(int precision, int ldw) {
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
     return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (kShInts + 2 * nw) * sizeof(int) +
-           (size_t)kSortN * (sizeof(int) + sizeof(float));
+           (size_t)kSortN * (sizeof(int) + sizeof(float)) + 8 + (size_t)kSortN * sizeof(double);
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

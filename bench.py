@@ -41,11 +41,11 @@ FP64_TFLOPS_NOMINAL = 1.25
 # DRAM bytes (read + write) per k_jacobi launch, from one ncu capture of this
 # workload on one stream (--chunk-streams 1, the launches the roofline's
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
-# five Jacobi launches of one step: 307.5, 38.9, 37.9, 29.0, 28.8 GB; averaged
+# five Jacobi launches of one step: 305.9, 39.2, 38.2, 29.3, 29.1 GB; averaged
 # per launch), keyed by the SHA-256 of the kernel source it was taken on.  Any
 # other source reports null: the counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "3830a466e7a42cc36f38076430aafe61d8f6d0fad59cfb37cbb2b925c565c153": 442.18e9 / 5,
+    "d341df5ac2db3da98727a8d7d6bedc15bd3646b6dadf83111324cac727d5b80a": 441.72e9 / 5,
 }
 
 

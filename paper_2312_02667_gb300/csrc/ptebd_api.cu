@@ -323,7 +323,7 @@ int launch_chain(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&
         y.w = a.w1;
         CUDA_TRY(st, wrap(PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
         CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_xform<R>(x, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(x, s); }));
+        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_orth<R>(x, s); }));
         CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_proj<R>(x, s); }));
         CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(y, s); }));
         CUDA_TRY(st, wrap(PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(y, s); }));
@@ -737,6 +737,7 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
     st->stream = static_cast<cudaStream_t>(stream);
     cudaGetDevice(&st->device);
     cudaError_t e = cfg->precision == PTEBD_FP64 ? jacobi_prepare<double>() : jacobi_prepare<float>();
+    if (e == cudaSuccess) e = cfg->precision == PTEBD_FP64 ? orth_prepare<double>() : orth_prepare<float>();
     if (e != cudaSuccess) {
         delete st;
         return PTEBD_ERR_CUDA;

@@ -97,6 +97,9 @@ template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStr
 template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s);
+// pass 1 of the tSU SVD: an orthonormal basis of the columns of X (ptebd_orth.cu)
+template <typename R> cudaError_t launch_orth(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t orth_prepare();   // raises its dynamic smem limit
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,
                                 int gated, double* totals, cudaStream_t s);
 // totals[0..2] += sum over c < k of partials[4 c + 0..2], in the order of c

@@ -41,11 +41,12 @@ FP64_TFLOPS_NOMINAL = 1.25
 # DRAM bytes (read + write) per k_jacobi launch, from one ncu capture of this
 # workload on one stream (--chunk-streams 1, the launches the roofline's
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
-# five Jacobi launches of one step: 305.9, 39.2, 38.2, 29.3, 29.1 GB; averaged
-# per launch), keyed by the SHA-256 of the kernel source it was taken on.  Any
-# other source reports null: the counters no longer describe the kernel.
+# three Jacobi launches of one step, the gated SVDs and the two tSU passes on
+# M^dag: 306.1, 40.2, 31.4 GB; averaged per launch), keyed by the SHA-256 of
+# the kernel source it was taken on.  Any other source reports null: the
+# counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "d341df5ac2db3da98727a8d7d6bedc15bd3646b6dadf83111324cac727d5b80a": 441.72e9 / 5,
+    "d341df5ac2db3da98727a8d7d6bedc15bd3646b6dadf83111324cac727d5b80a": 377.69e9 / 3,
 }
 
 
@@ -355,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
             "unit": "TFLOP/s",
             "frac": svd_rate / peak if peak else None,
             "traffic": jacobi_traffic() if args.precision == "mixed" and args.n_sites == 1024 and args.chi == 256 else None,
-            "traffic_note": "bytes per launch, averaged over the step's five Jacobi launches (gated 512x512 + four tSU passes); "
+            "traffic_note": "bytes per launch, averaged over the step's three Jacobi launches (gated 512x512 + two tSU passes on M^dag); "
                             "the blocked Jacobi streams every matrix past its register-resident 16-column block "
                             "nb(nb-1)/2 times per sweep, and 152 concurrent 2 MB matrices exceed L2",
             "algorithmic": "28 flop per column-pair-row visit x sweeps x n(n-1)/2 x m, counted on the device",

@@ -541,3 +541,27 @@ def test_bounded_wait_runs_out_reports_timeout_and_recovers(ptebd):
         fresh.apply_layer(gates, parity)
     for s in range(n):
         assert np.array_equal(st.site(s), fresh.site(s)), s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ptsu_with_dependent_columns_of_x(ptebd, prec):
+    # X = Lambda Gamma_b Lambda of the tSU on bond b with two proportional
+    # columns: the Gram-Schmidt basis drops one of them; theta = X Y, and so its
+    # singular values (the new Lambda_b), must come out as the oracle's SVD of
+    # theta gives them.
+    n, chi = 10, 8
+    mps = oracle.canonicalize(inputs.random_mps_tensors(17, n, chi))
+    b = 4
+    g = mps.gammas[b].copy()                      # (2, chi_{b-1}, chi_b)
+    lam_b = mps.lambdas[b]
+    g[:, :, 1] = g[:, :, 0] * (lam_b[0] / lam_b[1]) * 0.5  # column 1 of X = column 0 / 2
+    mps.gammas[b] = g
+    st = ptebd.State(n, chi, prec, cutoff=1e-14)
+    load_into(st, mps)
+    ref = mps.copy()
+    st.regauge(1)
+    oracle.ptsu_step(ref, chi, thr(prec, 1e-14))
+    got = to_oracle(st)
+    for bb in range(n - 1):
+        compare_spectra(got.lambdas[bb], ref.lambdas[bb], TOL[prec], thr(prec, 1e-14), chi)
+    assert fidelity(got, mps) >= 1 - FTOL[prec]

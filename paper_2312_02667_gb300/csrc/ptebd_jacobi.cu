@@ -187,16 +187,18 @@ __device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigne
 
 
 __device__ __forceinline__ RotParams<float> rot_params(float al, float be, float gr, float gi, float g2) {
-    // MUFU reciprocal square roots; cos is refined by one Newton step so that
-    // cos^2 (1 + t^2) = 1 to rounding (the sign of the residual is not biased).
+    // t = 2 |g| sign(d) / (|d| + sqrt(d^2 + 4 |g|^2)), d = be - al: the smaller
+    // root of t^2 + (d / |g|) t - 1 = 0, formed without the quotient d / |g| (so
+    // with no overflow when |g| << |d|, and one reciprocal square root less on
+    // the chain).  MUFU reciprocal square roots; cos is refined by one Newton step
+    // so that cos^2 (1 + t^2) = 1 to rounding (the sign of the residual is not biased).
     const float ig = rsqrtf(g2);
     const float g = g2 * ig;
-    const float zeta = (be - al) * (0.5f * ig);
-    const float az = fabsf(zeta);
-    const float q0 = fmaf(zeta, zeta, 1.0f);
-    const float root = az < 1e15f ? q0 * rsqrtf(q0) : az;
-    float t = __fdividef(1.0f, az + root);
-    if (zeta < 0.0f) t = -t;
+    const float d = be - al;
+    const float h = fmaf(d, d, 4.0f * g2);
+    const float root = h * rsqrtf(h);
+    float t = __fdividef(2.0f * g, fabsf(d) + root);
+    if (d < 0.0f) t = -t;
     const float q = fmaf(t, t, 1.0f);
     float c = rsqrtf(q);
     c = c * fmaf(-0.5f * q * c, c, 1.5f);
@@ -228,27 +230,55 @@ __device__ __forceinline__ RotParams<double> rot_params(double al, double be, do
 }
 
 
-// complex64 rotation of the pair with packed FP32 arithmetic: the same
-// operations as the scalar form, two components per instruction.
+// complex64 rotation of a pair of columns in the pair-split layout (PairRows):
+// the operations of the scalar form, applied to two rows per instruction.
 template <int RPL>
-__device__ __forceinline__ void rotate_packed(float2 (&a)[RPL], float2 (&b)[RPL], const RotParams<float>& p) {
-    const unsigned long long sr2 = pk2(p.sr, p.sr), cm2 = pk2(p.cm1, p.cm1);
-    const unsigned long long msr2 = pk2(-p.sr, -p.sr);
-    const unsigned long long msi_pm = pk2(-p.si, p.si);   // (-si, si)
+__device__ __forceinline__ void rotate_split(float2 (&a)[RPL], float2 (&b)[RPL], const RotParams<float>& p) {
+    const unsigned long long cm = pk2(p.cm1, p.cm1);
+    const unsigned long long sr = pk2(p.sr, p.sr), msr = pk2(-p.sr, -p.sr);
+    const unsigned long long si = pk2(p.si, p.si), msi = pk2(-p.si, -p.si);
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        const unsigned long long A = pk2(a[q].x, a[q].y), B = pk2(b[q].x, b[q].y);
-        const unsigned long long As = pk2(a[q].y, a[q].x), Bs = pk2(b[q].y, b[q].x);
-        // -(sr br + si bi, sr bi - si br)
-        const unsigned long long tneg = fma2(msi_pm, Bs, mul2(msr2, B));
-        const unsigned long long an = add2(A, fma2(cm2, A, tneg));
-        // (sr ar - si ai, sr ai + si ar)
-        const unsigned long long t2 = fma2(msi_pm, As, mul2(sr2, A));
-        const unsigned long long bn = add2(B, fma2(cm2, B, t2));
-        a[q] = upk2(an);
-        b[q] = upk2(bn);
+    for (int h = 0; h < RPL / 2; ++h) {
+        const unsigned long long ax = pk2(a[2 * h].x, a[2 * h].y), ay = pk2(a[2 * h + 1].x, a[2 * h + 1].y);
+        const unsigned long long bx = pk2(b[2 * h].x, b[2 * h].y), by = pk2(b[2 * h + 1].x, b[2 * h + 1].y);
+        const unsigned long long t1 = fma2(msi, by, mul2(msr, bx));  // -(sr br + si bi)
+        const unsigned long long t2 = fma2(si, bx, mul2(msr, by));   // -(sr bi - si br)
+        const unsigned long long t3 = fma2(msi, ay, mul2(sr, ax));   // sr ar - si ai
+        const unsigned long long t4 = fma2(si, ax, mul2(sr, ay));    // sr ai + si ar
+        a[2 * h] = upk2(add2(ax, fma2(cm, ax, t1)));
+        a[2 * h + 1] = upk2(add2(ay, fma2(cm, ay, t2)));
+        b[2 * h] = upk2(add2(bx, fma2(cm, bx, t3)));
+        b[2 * h + 1] = upk2(add2(by, fma2(cm, by, t4)));
     }
 }
+// a^H b in the pair-split layout, scalar FMAs with one partial sum per row of
+// the pair (packed FP32 instructions measured slower here than in the rotation)
+template <int RPL>
+__device__ __forceinline__ void dot_split(const float2 (&a)[RPL], const float2 (&b)[RPL], float& gr, float& gi) {
+    float gr0 = 0, gr1 = 0, gi0 = 0, gi1 = 0;
+#pragma unroll
+    for (int h = 0; h < RPL / 2; ++h) {
+        const float2 ar = a[2 * h], ai = a[2 * h + 1], br = b[2 * h], bi = b[2 * h + 1];
+        gr0 = fmaf(ar.x, br.x, gr0); gr0 = fmaf(ai.x, bi.x, gr0);
+        gi0 = fmaf(ar.x, bi.x, gi0); gi0 = fmaf(-ai.x, br.x, gi0);
+        gr1 = fmaf(ar.y, br.y, gr1); gr1 = fmaf(ai.y, bi.y, gr1);
+        gi1 = fmaf(ar.y, bi.y, gi1); gi1 = fmaf(-ai.y, br.y, gi1);
+    }
+    gr = gr0 + gr1;
+    gi = gi0 + gi1;
+}
+
+// Rows of a column held by a lane, RPL entries per lane.  complex64 with RPL >= 2
+// (rows even): the column is kept in a pair-split layout while the sweeps run,
+// every two rows r, r + 1 (r even) stored as (Re r, Re r+1, Im r, Im r+1), so that
+// one 16-byte access moves the pair and the packed FP32 instructions find the real
+// parts and the imaginary parts of the pair in one register pair each.  Lane
+// `lane` holds the pairs r = 64 h + 2 lane, h = 0 .. RPL/2 - 1: entry 2 h is
+// (Re r, Re r+1), entry 2 h + 1 is (Im r, Im r+1).  Otherwise entry q is row
+// 32 q + lane as a complex number.
+template <typename C, int RPL> struct PairRows {
+    static constexpr bool on = std::is_same<C, float2>::value && RPL >= 2;
+};
 
 template <typename R, int RPL>
 __device__ __forceinline__ R col_norm2(const cx_t<R> (&a)[RPL]) {
@@ -266,24 +296,33 @@ __device__ __forceinline__ R col_norm2(const cx_t<R> (&a)[RPL]) {
 // are updated.  Returns true if it rotated.
 template <typename R, int RPL>
 __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R& al, R& be, R tol2) {
-    R gr0 = 0, gr1 = 0, gi0 = 0, gi1 = 0;  // a^H b, two partial sums each
+    constexpr bool split = PairRows<cx_t<R>, RPL>::on;
+    R gr, gi;  // a^H b
+    if constexpr (split) {
+        dot_split<RPL>(a, b, gr, gi);
+    } else {
+        R gr0 = 0, gr1 = 0, gi0 = 0, gi1 = 0;  // two partial sums each
 #pragma unroll
-    for (int q = 0; q < RPL; ++q) {
-        if (q & 1) {
-            gr1 = fma(a[q].x, b[q].x, gr1); gr1 = fma(a[q].y, b[q].y, gr1);
-            gi1 = fma(a[q].x, b[q].y, gi1); gi1 = fma(-a[q].y, b[q].x, gi1);
-        } else {
-            gr0 = fma(a[q].x, b[q].x, gr0); gr0 = fma(a[q].y, b[q].y, gr0);
-            gi0 = fma(a[q].x, b[q].y, gi0); gi0 = fma(-a[q].y, b[q].x, gi0);
+        for (int q = 0; q < RPL; ++q) {
+            if (q & 1) {
+                gr1 = fma(a[q].x, b[q].x, gr1); gr1 = fma(a[q].y, b[q].y, gr1);
+                gi1 = fma(a[q].x, b[q].y, gi1); gi1 = fma(-a[q].y, b[q].x, gi1);
+            } else {
+                gr0 = fma(a[q].x, b[q].x, gr0); gr0 = fma(a[q].y, b[q].y, gr0);
+                gi0 = fma(a[q].x, b[q].y, gi0); gi0 = fma(-a[q].y, b[q].x, gi0);
+            }
         }
+        gr = gr0 + gr1;
+        gi = gi0 + gi1;
     }
-    const R gr = warp_sum(gr0 + gr1), gi = warp_sum(gi0 + gi1);
+    gr = warp_sum(gr);
+    gi = warp_sum(gi);
     if (!(al > 0) || !(be > 0)) return false;
     const R g2 = gr * gr + gi * gi;
     if (!(g2 > (tol2 * al) * be)) return false;
     const RotParams<R> p = rot_params(al, be, gr, gi, g2);
-    if constexpr (std::is_same<R, float>::value) {
-        rotate_packed<RPL>(a, b, p);
+    if constexpr (split) {
+        rotate_split<RPL>(a, b, p);
     } else {
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -305,12 +344,6 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
 }
 
 
-// Rows of a column held by a lane, RPL entries per lane.  complex64 with RPL >= 2:
-// entry q is row 64 (q / 2) + 2 lane + (q & 1), adjacent rows in pairs, moved
-// with 16-byte accesses; otherwise entry q is row 32 q + lane.
-template <typename C, int RPL> struct PairRows {
-    static constexpr bool on = std::is_same<C, float2>::value && RPL >= 2;
-};
 template <typename C, int RPL>
 __device__ __forceinline__ int lane_row(int lane, int q) {
     return PairRows<C, RPL>::on ? 64 * (q >> 1) + 2 * lane + (q & 1) : 32 * q + lane;
@@ -416,6 +449,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     int cur = 0;
     int sweep = 0;
     long long rot_total = 0;
+    int rot_w = 0;  // rotations of this warp in the sweep
     bool converged = false;
 
     auto issue_load = [&](int J, int buf) {
@@ -423,8 +457,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         const int c0 = J * NW;
         const int nreal = min(NW, cols - c0);
         mbar_expect_tx(&bar[buf], (uint32_t)nreal * col_bytes);
-        for (int c = 0; c < nreal; ++c)
-            bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)cperm[c0 + c] * ldw, col_bytes, &bar[buf]);
+        for (int c = 0; c < nreal; ++c) {
+            const int gc = cperm[c0 + c];
+            bulk_g2s(bufJ[buf] + (size_t)c * mpad, W + (size_t)gc * ldw, col_bytes, &bar[buf]);
+            jn2[buf * NW + c] = (R)nrm2[gc];  // the tracked norm the column enters the stage with
+        }
         sh[3 + buf] = 1;
         sh[5 + buf] = (int)phase[buf];
     };
@@ -441,16 +478,30 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     };
 
     // exact squared column norms (each warp its columns c = warp mod NW); with
-    // want_max, the exponent of the largest |entry| is gathered in sh[2] as well
-    auto norm_pass = [&](bool want_max) {
+    // want_max, the exponent of the largest |entry| is gathered in sh[2] as well.
+    // A squared norm is the sum of the squares of all the column's floats, so it
+    // does not depend on the layout.  With to_split (PairRows only) the columns are
+    // rewritten in the pair-split layout on the way.
+    auto norm_pass = [&](bool want_max, bool to_split) {
         R mx = 0;
         for (int c = warp; c < cols; c += NW) {
             R s0 = 0, s1 = 0;
-            for (int r = lane; r < rows; r += 32) {
-                const C v = W[(size_t)c * ldw + r];
-                s0 = fma(v.x, v.x, s0);
-                s1 = fma(v.y, v.y, s1);
-                if (want_max) mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            if constexpr (PairRows<C, RPL>::on) {
+                float4* col = reinterpret_cast<float4*>(W + (size_t)c * ldw);
+                for (int g = lane; g < rows / 2; g += 32) {
+                    float4 v = col[g];
+                    s0 = fma(v.x, v.x, s0); s1 = fma(v.y, v.y, s1);
+                    s0 = fma(v.z, v.z, s0); s1 = fma(v.w, v.w, s1);
+                    if (want_max) mx = fmax(mx, fmax(fmax(fabs(v.x), fabs(v.y)), fmax(fabs(v.z), fabs(v.w))));
+                    if (to_split) col[g] = make_float4(v.x, v.z, v.y, v.w);
+                }
+            } else {
+                for (int r = lane; r < rows; r += 32) {
+                    const C v = W[(size_t)c * ldw + r];
+                    s0 = fma(v.x, v.x, s0);
+                    s1 = fma(v.y, v.y, s1);
+                    if (want_max) mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+                }
             }
             const R s2 = warp_sum(s0 + s1);
             if (lane == 0) nrm2[c] = (double)s2;
@@ -459,6 +510,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             mx = warp_max(mx);
             if (lane == 0) atomicMax(&sh[2], exp_key<R>(mx));
         }
+        if (to_split) fence_async_global();  // the sweeps read W through TMA as well
     };
     // Range guard.  Squared norms and |a^H b|^2 are formed in R: with entries of
     // 2^range_e and more they can overflow (and with tiny entries underflow), which
@@ -471,7 +523,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
         if (tid == 0) { sh[0] = 0; bulk_wait_all(); fence_async_global(); }
         __syncthreads();
-        norm_pass(sweep == 0);
+        norm_pass(sweep == 0, sweep == 0 && PairRows<C, RPL>::on);
         __syncthreads();
         if (sweep == 0) {
             const int ex = sh[2] - kExpOffset;  // 2^ex <= max |entry| < 2^(ex + 1)
@@ -486,7 +538,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     }
                 fence_async_global();  // the sweeps read W through TMA as well
                 __syncwarp();
-                norm_pass(false);
+                norm_pass(false, false);
                 __syncthreads();
             }
         }
@@ -541,8 +593,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             if (lane == 0) {
                                 in2[p] = nx;
                                 in2[q2] = ny;
-                                atomicAdd(&sh[0], 1);
                             }
+                            ++rot_w;
                         }
                     }
                 }
@@ -573,31 +625,28 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     int* done = slot_done + cur * NW;
                     R* sn2 = jn2 + cur * NW;
                     const int base = jblocks[cur] * NW;
+                    const bool test_wait = A.wait_test && warp == 0 && sweep == 0 && I == 0 && J == 1;
                     for (int r = 0; r < NW && ok; ++r) {
                         const int jc = (warp + r) & (NW - 1);
                         const int lcol = J * NW + jc;
                         if (r > 0) {
-                            if (A.wait_test && warp == 0 && r == 1 && sweep == 0 && I == 0 && J == 1)
-                                ok = counter_wait_bounded(&done[jc], 0x7fffffff, &sh[1], 1ll << 20);
-                            else
-                                ok = counter_wait_bounded(&done[jc], base + r, &sh[1]);
+                            const bool t = test_wait && r == 1;
+                            ok = counter_wait_bounded(&done[jc], t ? 0x7fffffff : base + r, &sh[1],
+                                                      t ? (1ll << 20) : (1ll << 31));
                         }
                         if (!ok) break;
                         if (lcol < cols) {
-                            const int gcol = cperm[lcol];  // physical column
-                            R be = (r == 0) ? (R)nrm2[gcol] : sn2[jc];
+                            R be = sn2[jc];
                             if (mine) {
                                 C y[RPL];
                                 slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                 if (pair_rotate<R, RPL>(a, y, al, be, tol2)) {
                                     slot_store<C, RPL>(y, buf + (size_t)jc * mpad, lane);
-                                    if (lane == 0) atomicAdd(&sh[0], 1);
+                                    ++rot_w;
                                 }
                             }
-                            if (lane == 0) {
-                                sn2[jc] = be;
-                                if (r == NW - 1) nrm2[gcol] = (double)be;
-                            }
+                            sn2[jc] = be;  // every lane: the same value
+                            if (r == NW - 1) nrm2[cperm[lcol]] = (double)be;
                         }
                         __syncwarp();
                         if (lane == 0) counter_release_add(&done[jc]);
@@ -630,6 +679,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             fence_async_global();
             __syncthreads();
         }
+        if (lane == 0 && rot_w) atomicAdd(&sh[0], rot_w);
+        rot_w = 0;
         __syncthreads();
         const int rot = sh[0];
         rot_total += rot;
@@ -653,18 +704,32 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             atomicAdd(&A.work[7], 1ull);
         }
     }
-    // FP64 column norms = singular values; the range guard's scaling is undone
+    // FP64 column norms = singular values; the range guard's scaling is undone and
+    // the pair-split layout turned back into plain complex columns
     double* nrm = A.norms + (size_t)j * ldw;
     const R unscale = ldexp((R)1, scale_e);
     for (int c = warp; c < cols; c += NW) {
         double acc = 0.0;
-        for (int r = lane; r < rows; r += 32) {
-            C v = W[(size_t)c * ldw + r];
-            acc = fma((double)v.x, (double)v.x, acc);
-            acc = fma((double)v.y, (double)v.y, acc);
-            if (scale_e != 0) {
-                v.x *= unscale; v.y *= unscale;
-                W[(size_t)c * ldw + r] = v;
+        if constexpr (PairRows<C, RPL>::on) {
+            float4* col = reinterpret_cast<float4*>(W + (size_t)c * ldw);
+            for (int g = lane; g < rows / 2; g += 32) {
+                float4 v = col[g];
+                acc = fma((double)v.x, (double)v.x, acc);
+                acc = fma((double)v.z, (double)v.z, acc);
+                acc = fma((double)v.y, (double)v.y, acc);
+                acc = fma((double)v.w, (double)v.w, acc);
+                if (scale_e != 0) { v.x *= unscale; v.y *= unscale; v.z *= unscale; v.w *= unscale; }
+                col[g] = make_float4(v.x, v.z, v.y, v.w);
+            }
+        } else {
+            for (int r = lane; r < rows; r += 32) {
+                C v = W[(size_t)c * ldw + r];
+                acc = fma((double)v.x, (double)v.x, acc);
+                acc = fma((double)v.y, (double)v.y, acc);
+                if (scale_e != 0) {
+                    v.x *= unscale; v.y *= unscale;
+                    W[(size_t)c * ldw + r] = v;
+                }
             }
         }
         acc = warp_sum(acc);

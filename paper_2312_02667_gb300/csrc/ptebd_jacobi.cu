@@ -231,9 +231,14 @@ __device__ __forceinline__ RotParams<double> rot_params(double al, double be, do
 
 
 // complex64 rotation of a pair of columns in the pair-split layout (PairRows):
-// the operations of the scalar form, applied to two rows per instruction.
-template <int RPL>
-__device__ __forceinline__ void rotate_split(float2 (&a)[RPL], float2 (&b)[RPL], const RotParams<float>& p) {
+// the operations of the scalar form, applied to two rows per instruction.  With
+// SA / SB the rotated rows of a / b also go to the shared-memory slot as / bs as
+// soon as they are formed, so that the stores are under way before the rotation
+// ends (a warp hands a column on only once its stores are complete).
+template <int RPL, bool SA, bool SB>
+__device__ __forceinline__ void rotate_split(float2 (&a)[RPL], float2 (&b)[RPL], const RotParams<float>& p,
+                                             float2* as, float2* bs) {
+    const int lane = threadIdx.x & 31;
     const unsigned long long cm = pk2(p.cm1, p.cm1);
     const unsigned long long sr = pk2(p.sr, p.sr), msr = pk2(-p.sr, -p.sr);
     const unsigned long long si = pk2(p.si, p.si), msi = pk2(-p.si, -p.si);
@@ -249,6 +254,12 @@ __device__ __forceinline__ void rotate_split(float2 (&a)[RPL], float2 (&b)[RPL],
         a[2 * h + 1] = upk2(add2(ay, fma2(cm, ay, t2)));
         b[2 * h] = upk2(add2(bx, fma2(cm, bx, t3)));
         b[2 * h + 1] = upk2(add2(by, fma2(cm, by, t4)));
+        if constexpr (SB)
+            *reinterpret_cast<float4*>(bs + 64 * h + 2 * lane) =
+                make_float4(b[2 * h].x, b[2 * h].y, b[2 * h + 1].x, b[2 * h + 1].y);
+        if constexpr (SA)
+            *reinterpret_cast<float4*>(as + 64 * h + 2 * lane) =
+                make_float4(a[2 * h].x, a[2 * h].y, a[2 * h + 1].x, a[2 * h + 1].y);
     }
 }
 // a^H b in the pair-split layout, scalar FMAs with one partial sum per row of
@@ -291,11 +302,16 @@ __device__ __forceinline__ R col_norm2(const cx_t<R> (&a)[RPL]) {
     return warp_sum(s0 + s1);
 }
 
+template <typename C, int RPL>
+__device__ __forceinline__ void slot_store(const C (&v)[RPL], C* col, int lane);
+
 // Rotate the column pair (a, b) held by one warp (RPL entries per lane) if it is
 // not yet orthogonal to within tol; al and be are their tracked squared norms and
-// are updated.  Returns true if it rotated.
-template <typename R, int RPL>
-__device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R& al, R& be, R tol2) {
+// are updated.  Returns true if it rotated; then, with SA / SB, the rotated a / b
+// have been written to the shared-memory slot as / bs as well.
+template <typename R, int RPL, bool SA, bool SB>
+__device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R& al, R& be, R tol2,
+                                            cx_t<R>* as, cx_t<R>* bs) {
     constexpr bool split = PairRows<cx_t<R>, RPL>::on;
     R gr, gi;  // a^H b
     if constexpr (split) {
@@ -322,7 +338,7 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     if (!(g2 > (tol2 * al) * be)) return false;
     const RotParams<R> p = rot_params(al, be, gr, gi, g2);
     if constexpr (split) {
-        rotate_split<RPL>(a, b, p);
+        rotate_split<RPL, SA, SB>(a, b, p, as, bs);
     } else {
 #pragma unroll
     for (int q = 0; q < RPL; ++q) {
@@ -332,6 +348,8 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
         b[q].x = br + (p.cm1 * br + (p.sr * ar - p.si * ai));
         b[q].y = bi + (p.cm1 * bi + (p.sr * ai + p.si * ar));
     }
+    if constexpr (SB) slot_store<cx_t<R>, RPL>(b, bs, threadIdx.x & 31);
+    if constexpr (SA) slot_store<cx_t<R>, RPL>(a, as, threadIdx.x & 31);
     }
     // norms from the 2x2 problem; the one that shrinks is recomputed when it
     // lost most of its size (cancellation in the update)
@@ -586,9 +604,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         slot_load<C, RPL>(x, bufI + (size_t)p * mpad, lane);
                         slot_load<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
                         R nx = in2[p], ny = in2[q2];
-                        if (pair_rotate<R, RPL>(x, y, nx, ny, tol2)) {
-                            slot_store<C, RPL>(x, bufI + (size_t)p * mpad, lane);
-                            slot_store<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
+                        if (pair_rotate<R, RPL, true, true>(x, y, nx, ny, tol2, bufI + (size_t)p * mpad,
+                                                            bufI + (size_t)q2 * mpad)) {
                             __syncwarp();
                             if (lane == 0) {
                                 in2[p] = nx;
@@ -640,12 +657,13 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             if (mine) {
                                 C y[RPL];
                                 slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
-                                if (pair_rotate<R, RPL>(a, y, al, be, tol2)) {
-                                    slot_store<C, RPL>(y, buf + (size_t)jc * mpad, lane);
+                                // the rotated J column goes back to its slot inside the rotation
+                                if (pair_rotate<R, RPL, false, true>(a, y, al, be, tol2, nullptr,
+                                                                     buf + (size_t)jc * mpad)) {
+                                    sn2[jc] = be;  // every lane: the same value
                                     ++rot_w;
                                 }
                             }
-                            sn2[jc] = be;  // every lane: the same value
                             if (r == NW - 1) nrm2[cperm[lcol]] = (double)be;
                         }
                         __syncwarp();

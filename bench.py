@@ -42,11 +42,11 @@ FP64_TFLOPS_NOMINAL = 1.25
 # workload on one stream (--chunk-streams 1, the launches the roofline's
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
 # three Jacobi launches of one step, the gated SVDs and the two tSU passes on
-# M^dag: 306.1, 40.2, 31.4 GB; averaged per launch), keyed by the SHA-256 of
+# M^dag: 309.5, 41.6, 32.8 GB; averaged per launch), keyed by the SHA-256 of
 # the kernel source it was taken on.  Any other source reports null: the
 # counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "d341df5ac2db3da98727a8d7d6bedc15bd3646b6dadf83111324cac727d5b80a": 377.69e9 / 3,
+    "1730e1813e420fcb493e161b8162f875ee85b7723d2198dca10b9358b688dedd": 383.91e9 / 3,
 }
 
 

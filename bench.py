@@ -43,19 +43,27 @@ FP64_TFLOPS_NOMINAL = 1.25
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
 # three Jacobi launches of one step, the gated SVDs and the two tSU passes on
 # M^dag: 309.5, 41.6, 32.8 GB; averaged per launch), keyed by the SHA-256 of
-# the kernel source it was taken on.  Any other source reports null: the
+# the kernel source it was taken on, with comments and blank lines removed (a
+# comment edit leaves the key alone).  Any other code reports null: the
 # counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "1730e1813e420fcb493e161b8162f875ee85b7723d2198dca10b9358b688dedd": 383.91e9 / 3,
+    "3307a5e1945a606f5f81bcee19e3e0422f0b5697a455458e6f3c96282bd8f35c": 383.91e9 / 3,
 }
 
 
-def jacobi_traffic():
+def code_digest(text):
+    """SHA-256 of C++ source with // comments, trailing blanks and empty lines removed."""
     import hashlib
+    import re
+    lines = [ln.rstrip() for ln in re.sub(r"//[^\n]*", "", text).splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()
+
+
+def jacobi_traffic():
     path = os.path.join(ROOT, "paper_2312_02667_gb300", "csrc", "ptebd_jacobi.cu")
     try:
-        with open(path, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        with open(path, encoding="utf-8") as f:
+            digest = code_digest(f.read())
     except OSError:
         return None
     return JACOBI_TRAFFIC.get(digest)

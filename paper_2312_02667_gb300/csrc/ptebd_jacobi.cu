@@ -3,13 +3,15 @@
 //
 // One CTA per bond.  The matrix w (rows x cols, column-major, rows >= cols)
 // stays in global memory / L2; the CTA sweeps over blocks of NW columns:
-//   * block I is held in registers, one column per warp (lane l holds rows
-//     l, l+32, ...);
+//   * block I is held in registers, one column per warp (which rows a lane
+//     holds: PairRows below; complex64 columns are kept pair-split while the
+//     sweeps run and turned back into plain complex columns at the end);
 //   * the intra-block pairs of I are rotated in shared memory (round-robin);
 //   * every later block J is streamed through a double-buffered shared-memory
 //     stage by TMA bulk copies (cp.async.bulk, completion on an mbarrier),
-//     rotated against I in NW rounds (warp w meets column (w + r) mod NW of J),
-//     and written back by a TMA bulk store.
+//     rotated against I in NW rounds (warp w meets column (w + r) mod NW of J,
+//     handed on from warp w + 1 once its rotated rows are in the stage), and
+//     written back by a TMA bulk store.
 // Each sweep therefore meets every column pair once (block row-cyclic order).
 // A pair (a, b) with |a^H b| > tol ||a|| ||b|| is rotated by the 2x2 unitary that
 // diagonalises its Gram matrix; the sweeps stop when none was rotated.  The

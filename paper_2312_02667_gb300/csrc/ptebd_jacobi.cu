@@ -14,7 +14,8 @@
 //     written back by a TMA bulk store.
 // Each sweep therefore meets every column pair once (block row-cyclic order).
 // A pair (a, b) with |a^H b| > tol ||a|| ||b|| is rotated by the 2x2 unitary that
-// diagonalises its Gram matrix; the sweeps stop when none was rotated.  The
+// diagonalises its Gram matrix; the sweeps stop when none was rotated (or, on
+// the complex64 path, when every rotation of a sweep was a small one: Eps).  The
 // squared column norms are recomputed at the start of every sweep and then
 // tracked through the rotations (a' and b' norms follow from the 2x2 problem),
 // so a pair costs one complex dot product; a norm that drops a lot is
@@ -116,6 +117,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // sqrt(rows) u ||a|| ||b|| after a rotation, so the factor must sit well above 1
 // or rounding keeps re-triggering rotations (more sweeps, and every extra
 // rotation adds rounding error to the columns).
+// early: the sweeps also stop after a sweep in which every rotated pair had
+// cos^2 = |a^H b|^2 / (|a|^2 |b|^2) below early * tol^2 (0 = only after a sweep
+// without rotations).  On the complex64 path the sweep after such a sweep was
+// measured never to meet a pair above 1.04 tol^2 (gated and tSU matrices of
+// saturated layers, Ginibre and graded spectra: thousands of SVDs), and to
+// spend itself on 0 to 2 rotations of pairs barely above tol, so it is skipped;
+// the columns are left orthogonal to about tol instead of below tol.
 template <typename R> struct Eps;
 // range_e: matrices whose largest entry is not in [2^-range_e, 2^range_e) are
 // rescaled before the sweeps (see the range guard in jacobi_body).
@@ -123,11 +131,13 @@ template <> struct Eps<float> {
     static constexpr double u = 5.9604644775390625e-08;  // 2^-24
     static constexpr double k = 8.0;
     static constexpr int range_e = 24;
+    static constexpr double early = 256.0;
 };
 template <> struct Eps<double> {
     static constexpr double u = 1.1102230246251565e-16;  // 2^-53
     static constexpr double k = 4.0;
     static constexpr int range_e = 240;
+    static constexpr double early = 0.0;
 };
 
 template <typename R>
@@ -310,10 +320,11 @@ __device__ __forceinline__ void slot_store(const C (&v)[RPL], C* col, int lane);
 // Rotate the column pair (a, b) held by one warp (RPL entries per lane) if it is
 // not yet orthogonal to within tol; al and be are their tracked squared norms and
 // are updated.  Returns true if it rotated; then, with SA / SB, the rotated a / b
-// have been written to the shared-memory slot as / bs as well.
+// have been written to the shared-memory slot as / bs as well, and big is set
+// if the pair's cos^2 was at least big2.
 template <typename R, int RPL, bool SA, bool SB>
 __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL], R& al, R& be, R tol2,
-                                            cx_t<R>* as, cx_t<R>* bs) {
+                                            R big2, bool& big, cx_t<R>* as, cx_t<R>* bs) {
     constexpr bool split = PairRows<cx_t<R>, RPL>::on;
     R gr, gi;  // a^H b
     if constexpr (split) {
@@ -338,6 +349,7 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     if (!(al > 0) || !(be > 0)) return false;
     const R g2 = gr * gr + gi * gi;
     if (!(g2 > (tol2 * al) * be)) return false;
+    big = big || (g2 > (big2 * al) * be);
     const RotParams<R> p = rot_params(al, be, gr, gi, g2);
     if constexpr (split) {
         rotate_split<RPL, SA, SB>(a, b, p, as, bs);
@@ -436,7 +448,7 @@ __device__ __forceinline__ void slot_store(const C (&v)[RPL], C* col, int lane) 
 // Columns are visited in order of decreasing norm, re-sorted at the start of
 // every sweep (de Rijk's ordering idea): it lowers the number of sweeps.
 constexpr int kSortN = 512;
-constexpr int kShInts = 7;  // shared ints ahead of the slot round counters
+constexpr int kShInts = 8;  // shared ints ahead of the slot round counters
 
 template <typename R, int NW, int RPL>
 __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int cols, int j, unsigned char* smem) {
@@ -451,7 +463,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     R* jn2 = reinterpret_cast<R*>(bar + 2);        // [2][NW]: tracked |col|^2 of the J stage slots
     R* in2 = jn2 + 2 * NW;                          // [NW]: |col|^2 of the I block (intra phase)
     // [0] rotations, [1] abort, [2] max exponent, [3..4] a load into the stage not yet
-    // waited for by thread 0, [5..6] the barrier phase that load completes
+    // waited for by thread 0, [5..6] the barrier phase that load completes, [7] a
+    // rotation in this sweep had cos^2 >= early tol^2
     int* sh = reinterpret_cast<int*>(in2 + NW);
     int* slot_done = sh + kShInts;  // [2][NW]: rounds completed on each column slot of each stage
     int* cperm = slot_done + 2 * NW;                                   // [kSortN]: sweep order -> column
@@ -463,6 +476,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
     const R tol2 = tol * tol;
+    const R big2 = (R)Eps<R>::early * tol2;
+    bool big_w = false;  // this warp rotated a pair with cos^2 >= big2 in the sweep
     const int nb = (cols + NW - 1) / NW;
     const uint32_t col_bytes = (uint32_t)(rows * sizeof(C));
     uint32_t phase[2] = {0u, 0u};
@@ -541,7 +556,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     int scale_e = 0;
 
     for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
-        if (tid == 0) { sh[0] = 0; bulk_wait_all(); fence_async_global(); }
+        if (tid == 0) { sh[0] = 0; sh[7] = 0; bulk_wait_all(); fence_async_global(); }
         __syncthreads();
         norm_pass(sweep == 0, sweep == 0 && PairRows<C, RPL>::on);
         __syncthreads();
@@ -606,7 +621,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         slot_load<C, RPL>(x, bufI + (size_t)p * mpad, lane);
                         slot_load<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
                         R nx = in2[p], ny = in2[q2];
-                        if (pair_rotate<R, RPL, true, true>(x, y, nx, ny, tol2, bufI + (size_t)p * mpad,
+                        if (pair_rotate<R, RPL, true, true>(x, y, nx, ny, tol2, big2, big_w, bufI + (size_t)p * mpad,
                                                             bufI + (size_t)q2 * mpad)) {
                             __syncwarp();
                             if (lane == 0) {
@@ -660,7 +675,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                                 C y[RPL];
                                 slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                 // the rotated J column goes back to its slot inside the rotation
-                                if (pair_rotate<R, RPL, false, true>(a, y, al, be, tol2, nullptr,
+                                if (pair_rotate<R, RPL, false, true>(a, y, al, be, tol2, big2, big_w, nullptr,
                                                                      buf + (size_t)jc * mpad)) {
                                     sn2[jc] = be;  // every lane: the same value
                                     ++rot_w;
@@ -700,12 +715,15 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             __syncthreads();
         }
         if (lane == 0 && rot_w) atomicAdd(&sh[0], rot_w);
+        if (lane == 0 && big_w) sh[7] = 1;
         rot_w = 0;
+        big_w = false;
         __syncthreads();
         const int rot = sh[0];
+        const bool small = Eps<R>::early > 0.0 && sh[7] == 0;
         rot_total += rot;
         __syncthreads();
-        if (rot == 0) { converged = true; ++sweep; break; }
+        if (rot == 0 || small) { converged = true; ++sweep; break; }
     }
     if (tid == 0) { bulk_wait_all(); fence_async_global(); }
     __syncthreads();

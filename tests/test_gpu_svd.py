@@ -42,6 +42,30 @@ def test_ginibre_512(env, prec, tol):
         assert np.abs(np.linalg.norm(rows, axis=1) - sig[i]).max() <= tol * 10 * ref[0]
 
 
+def test_mixed_columns_orthogonal_to_the_threshold(env):
+    # The complex64 sweeps stop after a sweep without rotations or after one whose
+    # rotations all had cos^2 < 256 tol^2 (tol = 8 sqrt(m) u, the rotation
+    # threshold).  Either way every pair of output columns must be orthogonal to
+    # about tol: the largest |u_i^H u_j| (unit columns, formed in complex128 from
+    # the stored complex64 U) stays below 1.5 tol.  A stopping rule that quit in
+    # the quadratic phase (cos ~ 1e-3) would leave pairs far above it.
+    torch, ptebd = env
+    rng = np.random.default_rng(11)
+    m = 512
+    tol = 8.0 * np.sqrt(m) * 2.0 ** -24
+    gin = (rng.standard_normal((2, m, m)) + 1j * rng.standard_normal((2, m, m))) / np.sqrt(2 * m)
+    lam = 10.0 ** (-6.0 * np.arange(m) / m)
+    graded = np.stack([haar(m, rng) @ np.diag(lam) @ haar(m, rng).conj().T for _ in range(2)])
+    a = np.concatenate([gin, graded])
+    _, u = ptebd.svd_batched(torch.from_numpy(a).to(torch.complex64).cuda(), want_u=True)
+    u = u.cpu().numpy().astype(np.complex128)
+    for i in range(a.shape[0]):
+        ui = u[i] / np.linalg.norm(u[i], axis=0)[None, :]
+        g = np.abs(ui.conj().T @ ui)
+        np.fill_diagonal(g, 0.0)
+        assert g.max() <= 1.5 * tol, (i, g.max() / tol)
+
+
 @pytest.mark.parametrize("prec,shifts", [("mixed", [-100, -40, 40, 100]), ("fp64", [-700, 600])])
 def test_range_guard_scale_invariance(env, prec, shifts):
     # sigma(2^k A) = 2^k sigma(A): the kernel forms squared norms and |a^H b|^2 in

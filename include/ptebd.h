@@ -279,6 +279,12 @@ int ptebd_batch_apply_layer(ptebd_batch* b, const double* const* gates, const in
  *    descending order (FP64 norms of the rotated columns).
  * u: device or NULL; when given, batch x (ldu x cols) complex of the input
  *    type, column k = the left singular vector of sigma[k] (zero if sigma[k] = 0).
+ * Accuracy: the columns of U are orthogonal to about tol = k sqrt(rows) u
+ *    (k = 4 and u = 2^-53 for complex128; k = 8 and u = 2^-24 for complex64).
+ *    The sweeps stop after a sweep in which no pair had |cos| > tol, or, for
+ *    complex64, after a sweep whose rotated pairs all had cos^2 < 256 tol^2
+ *    (the sweep after such a sweep was measured to find no pair above
+ *    1.04 tol^2).
  * workspace: device, 256-byte aligned, at least ptebd_svd_workspace_bytes.
  * The input is not modified.  Runs on `stream` (cudaStream_t).  check != 0
  * synchronises the stream and reports device errors (sweep limit, non-finite

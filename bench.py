@@ -85,6 +85,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64-side", action="store_true", help="skip the mixed-vs-FP64 side measurement")
     p.add_argument("--chunk-streams", type=int, default=0, help="bond chunks per layer (0: the library's choice)")
+    p.add_argument("--serving", action="store_true",
+                   help="the batched-serving workload (64 uneven circuits, one graph launch per layer) alone")
+    p.add_argument("--routed", action="store_true",
+                   help="the 2D routed workload (32x32 lattice, depth 8, chi 128, compiled sparse layers) alone")
     p.add_argument("--svd-only", action="store_true",
                    help="micro benchmark instead: the batched Jacobi SVD on 512x512 complex64 matrices")
     return p.parse_args()
@@ -494,10 +498,117 @@ def svd_micro(args):
     return out
 
 
+def _timed_run(reset, body):
+    """Wall time of body() on reset states, synchronised on both sides, and the
+    CUDA-event time on the current stream (the states' stream)."""
+    import torch
+    reset()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record()
+    body()
+    e1.record()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3
+
+
+def serving_bench(args):
+    """Batched serving: 64 independent 1D brickwork circuits of Haar U(4) gates,
+    N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256} (the seeded
+    recipe of the batched-serving test), mixed precision, g = 0, advanced together
+    by one CUDA-graph launch per layer (ptebd_batch_apply_layer; gates from host
+    memory).  One untimed pass records the graphs; the timed pass runs the whole
+    set again from reset states."""
+    import numpy as np
+    import torch
+
+    from paper_2312_02667_gb300 import inputs, ptebd
+    rng = np.random.default_rng(64)
+    k = 64
+    ns = rng.integers(50, 501, k)
+    ds = rng.integers(8, 25, k)
+    chis = rng.choice([32, 64, 128, 256], k)
+    states = [ptebd.State(int(ns[i]), int(chis[i]), "mixed") for i in range(k)]
+    circuits_ = [inputs.brickwork_circuit(300 + i, int(ns[i]), int(ds[i]), circuit=i) for i in range(k)]
+    layers, gated = [], 0
+    for layer in range(int(ds.max())):
+        gl, par = [], []
+        for i in range(k):
+            if layer < ds[i]:
+                parity, bonds, gates = circuits_[i][layer]
+                gl.append(gates)
+                par.append(parity)
+                gated += len(bonds)
+            else:
+                gl.append(None)
+                par.append(-1)
+        layers.append((gl, par))
+    batch = ptebd.Batch(states)
+
+    def reset():
+        for st in states:
+            st.reset()
+
+    def body():
+        for gl, par in layers:
+            batch.apply_layer(gl, par)
+
+    first, _ = _timed_run(reset, body)
+    wall, dev = _timed_run(reset, body)
+    batch.close()
+    return {"metric": "batched serving: 64 uneven 1D circuits, one graph launch per layer", "unit": "bond-SVDs/s",
+            "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
+            "circuit_layers_per_s": float(ds.sum()) / wall, "batch_layers_per_s": len(layers) / wall,
+            "wall_s": wall, "device_s": dev, "first_pass_s": first, "gated_bond_updates": gated,
+            "circuits": k, "circuit_layers": int(ds.sum()), "batch_layers": len(layers),
+            "config": {"workload": "64 circuits, N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256}, "
+                                   "Haar U(4) brickwork, cutoff 1e-12, mixed, g = 0, from |0...0>",
+                       "seed": 64}}
+
+
+def routed_bench(args):
+    """The 2D routed workload: a 32x32 lattice on the snake path (1024 qubits),
+    8 physical layers of Haar U(4) gates in the ABCD pattern compiled to 194
+    sparse layers (the C/D pairs through SWAP networks, SWAPs merged into the
+    gates), chi_max = 128, mixed, each compiled layer through ptebd_apply_bonds
+    (gates from host memory).  Timed from |0...0> over the whole circuit (the
+    paper's total time / compiled depth), after one untimed pass."""
+    import torch
+
+    from paper_2312_02667_gb300 import circuits2d, ptebd
+    lx = ly = 32
+    chi = 128
+    compiled = circuits2d.compile_layers(lx, ly, circuits2d.physical_layers(4, lx, ly, 8))
+    st = ptebd.State(lx * ly, chi, "mixed")
+    gated = sum(len(b) for b, _ in compiled)
+
+    def body():
+        for bonds, us in compiled:
+            st.apply_bonds(bonds, us)
+
+    first, _ = _timed_run(st.reset, body)
+    wall, dev = _timed_run(st.reset, body)
+    return {"metric": "2D routed circuit, 32x32 lattice, depth 8, chi 128", "unit": "bond-SVDs/s",
+            "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
+            "ms_per_compiled_layer": 1e3 * wall / len(compiled), "compiled_layers": len(compiled),
+            "gated_bond_updates": gated, "wall_s": wall, "device_s": dev, "first_pass_s": first,
+            "max_chi": int(max(st.chi())),
+            "config": {"workload": "32x32 lattice on the snake path, 8 physical layers (ABCD) of Haar U(4) gates, "
+                                   "194 compiled layers, chi_max 128, cutoff 1e-12, mixed, g = 0, from |0...0>",
+                       "seed": 4}}
+
+
 def main():
     args = parse()
     if args.svd_only:
         print(json.dumps(svd_micro(args)), flush=True)
+        return
+    if args.serving:
+        print(json.dumps(serving_bench(args)), flush=True)
+        return
+    if args.routed:
+        print(json.dumps(routed_bench(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

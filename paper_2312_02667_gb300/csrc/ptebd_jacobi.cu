@@ -346,7 +346,9 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     }
     gr = warp_sum(gr);
     gi = warp_sum(gi);
-    if (!(al > 0) || !(be > 0)) return false;
+    // al, be >= 0 (a tracked norm that shrinks a lot is recomputed from its
+    // column), so a zero column (g = 0) or a non-finite value fails this test
+    // and is left alone
     const R g2 = gr * gr + gi * gi;
     if (!(g2 > (tol2 * al) * be)) return false;
     big = big || (g2 > (big2 * al) * be);

@@ -42,12 +42,12 @@ FP64_TFLOPS_NOMINAL = 1.25
 # workload on one stream (--chunk-streams 1, the launches the roofline's
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
 # three Jacobi launches of one step, the gated SVDs and the two tSU passes on
-# M^dag: 291.2, 39.2, 29.0 GB; averaged per launch), keyed by the SHA-256 of
+# M^dag: 291.2, 39.3, 28.9 GB; averaged per launch), keyed by the SHA-256 of
 # the kernel source it was taken on, with comments and blank lines removed (a
 # comment edit leaves the key alone).  Any other code reports null: the
 # counters no longer describe the kernel.
 JACOBI_TRAFFIC = {
-    "e831c4b750a8a348ab9014795ac528ebdd85ed68d2d67e59ce1e6b7f0f1b7b88": 359.41e9 / 3,
+    "a673d11c5d5a93dc1bb29eacc0981c712ff478a81a49b8f0917de1ae980a5fa0": 359.46e9 / 3,
 }
 
 

@@ -109,6 +109,41 @@ def test_norm_stability_2d(ptebd, name):
     assert rows[-1][2] < 1e-30, rows
 
 
+@pytest.mark.parametrize("n", [20, 24])
+def test_ptsu_distance_to_canonical_decreases(ptebd, n):
+    # The PtSU experiment of Sec. III D with our kernels: a canonicalised random
+    # MPS (entries a + ib, a and b uniform in [-1, 1]) with bond dimension chi,
+    # every bond truncated to chi/2 and the norm set to 1, then PtSU steps on the
+    # GPU (FP64) with C of Eq. (dist_to_cano) after each.  The paper reports
+    # that C falls rapidly and monotonically, faster for larger chi, and
+    # reaches zero after N/2 steps (Theorem 4).  One random MPS per case (the
+    # paper averages 100); the curves are printed (pytest -s).  The floor
+    # reached in FP64 is about 1e-10 rather than the oracle's 1e-13: the
+    # factor on the short side of each bond is rebuilt as S^-1 U^dag theta,
+    # which carries the rounding of theta scaled by sigma_1 / sigma_k.
+    from paper_2312_02667_gb300 import inputs
+    curves = {}
+    for chi in (32, 128, 256):
+        mps = oracle.canonicalize(inputs.random_mps_tensors(chi + n, n, chi))
+        cut = oracle.scale_to_unit_norm(oracle.truncate_all_bonds(mps, chi // 2))
+        st = ptebd.State(n, chi // 2, "fp64", cutoff=1e-14)
+        load_into(st, cut)
+        cs = [oracle.distance_to_canonical(cut)]
+        for _ in range(n // 2):
+            st.regauge(1)
+            cs.append(oracle.distance_to_canonical(to_oracle(st)))
+        curves[chi] = cs
+        print(f"N={n} chi={chi}: " + " ".join(f"{c:.2e}" for c in cs))
+        # monotone while above the floating-point floor, zero (to rounding) at N/2
+        for a, b in zip(cs, cs[1:]):
+            assert b <= a * (1 + 1e-6) or b < 1e-8, (chi, cs)
+        assert cs[0] > 0.1
+        assert cs[-1] < 1e-8, (chi, cs)
+    # larger chi: the canonical form is reached in fewer steps
+    steps = {chi: next(i for i, c in enumerate(cs) if c < 1e-8) for chi, cs in curves.items()}
+    assert steps[256] < steps[32], steps
+
+
 def test_run_cli_json_lines(ptebd, capsys):
     from paper_2312_02667_gb300 import run
     import json

@@ -38,6 +38,12 @@
  * discarded weight >= 1 in absolute mode, a Jacobi sweep limit, a bounded wait
  * that ran out) are latched in a device word and reported by the next
  * synchronising call (ptebd_sync, ptebd_norm, ptebd_get_*, ...).
+ * When a bounded wait runs out, the CTA waits (bounded again) for its own bulk
+ * copies before it returns; if even that wait runs out, copies into its shared
+ * memory may still be in flight when it returns, and the state is marked
+ * unusable: that report and every later call that would launch work or read
+ * results return PTEBD_ERR_TIMEOUT until the state is destroyed (ptebd_reset
+ * does not clear it).
  */
 #ifndef PTEBD_H
 #define PTEBD_H
@@ -91,10 +97,21 @@ typedef struct ptebd_config {
     int32_t g;          /* PtSU steps run after every layer (0 = none) */
     int32_t eps_mode;   /* enum ptebd_eps_mode */
     double cutoff;      /* drop singular values <= cutoff * lambda_1 (>= 0) */
-    double floor;       /* PTEBD_MIXED only: singular values <= floor * lambda_1
-                           are below what complex64 arithmetic resolves and are
-                           dropped as well; a negative value selects 1e-6.
-                           Ignored (treated as 0) for PTEBD_FP64. */
+    double resolve;     /* PTEBD_MIXED only (ignored for PTEBD_FP64): complex64
+                           singular values <= resolve * lambda_1 are not trusted
+                           (rounding leaves about 1e-7 lambda_1 where the exact
+                           spectrum has zeros); a negative value selects 1e-5.
+                           When resolve > cutoff, a gated or tSU bond whose kept
+                           count depends on such values (taken as real or as zero,
+                           with the structural bound rank(theta') <=
+                           rank(gate) chi_b) is recomputed in FP64 from the
+                           stored Gamma: theta' formed in FP64, FP64 Jacobi,
+                           truncation at the cutoff, Gamma rebuilt in FP64 and
+                           stored as complex64.  Every other bond is decided by
+                           the complex64 spectrum.  The configured cutoff is thus
+                           applied to FP64-accurate singular values wherever it
+                           decides the kept count.  When resolve <= cutoff nothing
+                           is recomputed. */
 } ptebd_config;
 
 typedef struct ptebd_state ptebd_state;
@@ -213,7 +230,8 @@ int ptebd_svd_sweeps(ptebd_state* st, int32_t* sweeps, int32_t* layers);
 #define PTEBD_K_GAMMA 3     /* Gamma_b and Gamma_{b+1} rebuild */
 #define PTEBD_K_REDUCE 4    /* per-layer eps / ln nu sums */
 #define PTEBD_K_FACTOR 5    /* tSU: X factor and theta^dag U_X */
-#define PTEBD_K_COUNT 6
+#define PTEBD_K_RESOLVE 6   /* PTEBD_MIXED: the FP64 pass over undecided bonds */
+#define PTEBD_K_COUNT 7
 int ptebd_timing(ptebd_state* st, int32_t enable);
 int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_kinds);
 
@@ -227,7 +245,10 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  * out[2] = Jacobi rotations actually applied;
  * out[3] = Jacobi sweeps summed over every SVD; out[4] = number of SVDs;
  * out[5..7] = the same three counts (visits, sweeps, SVDs) for the Jacobi runs
- * of the tSU steps alone.  n entries are written (<= 8). */
+ * of the tSU steps alone (out[0..7] count the state's own precision only);
+ * out[8] = bonds recomputed in FP64 by the resolution of a PTEBD_MIXED state
+ * (gated and tSU), out[9] = the Jacobi visits of those FP64 runs.
+ * n entries are written (<= 16; out[10..15] are reserved and read 0). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
 
 /* The end of Algorithm 1.  ptebd_canonicalize runs the PtSU steps that
@@ -308,9 +329,15 @@ int ptebd_svd_batched(int32_t precision, int32_t batch, int32_t rows, int32_t co
  * - A batch whose scratch (ptebd_svd_workspace_bytes) exceeds the array is
  *   rejected with PTEBD_ERR_MEMORY (e.g. at most 15 complex64 or 7 complex128
  *   matrices of 512 x 512 per call).
- * - The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.
+ * - `stream` must belong to the current device (PTEBD_ERR_INVALID otherwise);
+ *   every call looks the array's device address up on that device
+ *   (cudaGetSymbolAddress), so a context the caller tears down and re-creates
+ *   is handled.
+ * - The first call on each device loads the library's module holding the
+ *   array (the CUDA runtime loads modules lazily), which reserves the array
+ *   on that device: that call can fail with PTEBD_ERR_CUDA when the device is
+ *   out of memory, and it should be made before any stream capture, since
+ *   loading a module is not allowed while a stream is capturing.
  * - All calls share the array and it keeps the previous call's contents (the
  *   parts that must start at zero are cleared on every call): calls whose
  *   work overlaps on the GPU (two streams, two host threads) race on it and
@@ -319,6 +346,20 @@ int ptebd_svd_batched(int32_t precision, int32_t batch, int32_t rows, int32_t co
 int ptebd_svd_batched_noalloc(int32_t precision, int32_t batch, int32_t rows, int32_t cols,
                               const void* a, int32_t lda, double* sigma, void* u, int32_t ldu,
                               void* stream, int32_t check);
+
+/* Measured arithmetic peaks of this GPU (the paper has no counterpart: these
+ * are the roofline denominators of the kernels that run on the FP32 and FP64
+ * pipes).  kind 0: scalar FP32 FMA (fma.rn.f32); 1: packed FP32 FMA
+ * (fma.rn.f32x2, two FP32 lanes per instruction); 2: FP64 FMA.  One launch of
+ * 8 x (SM count) blocks of 256 threads, each thread running iters x 128 FMAs
+ * on 8 independent register chains (no memory traffic in the loop), after one
+ * untimed warm-up launch; *tflops = its flops (2 per FMA lane) over the CUDA
+ * event time on `stream`, *ms (may be NULL) = that time.  Synchronous.
+ * scratch: device memory of at least 8 x SMs x 256 x 8 bytes, which receives
+ * the per-thread results (written so that the arithmetic is kept).
+ * PTEBD_ERR_MEMORY when it is smaller. */
+int ptebd_alu_peak(int32_t kind, int32_t iters, void* scratch, size_t scratch_bytes, void* stream,
+                   double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -41,6 +42,10 @@ struct ptebd_state {
     cudaEvent_t fork_ev = nullptr;
     int chunk_streams = 0;  // requested number of chunks (0: chosen from N)
     int wait_test = 0;      // see ptebd_test_wait_timeout
+    // set once a device error says that a CTA returned with its own bulk copies still in
+    // flight (DERR_DRAIN): the state and its workspace can no longer be trusted, and
+    // every later call that launches work on it fails until it is destroyed
+    bool poisoned = false;
     ~ptebd_state() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
@@ -53,10 +58,22 @@ namespace ptebd {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Complex64 singular values below 1e-5 sigma_1 are not trusted by default: the
+// rounding of theta' and of the rotations leaves values of about 1e-7 sigma_1
+// where the exact spectrum has zeros.
+constexpr double kResolveDefault = 1e-5;
+
 static int chip_for(int chi_max) {
     int c = 16;
     while (c < chi_max) c <<= 1;
     return c;
+}
+
+// PTEBD_MIXED: the relative level below which complex64 singular values are not
+// trusted (the config's `resolve`, negative = the default).
+double resolve_level(const ptebd_config& c) {
+    if (c.precision != PTEBD_MIXED) return 0.0;
+    return c.resolve < 0.0 ? kResolveDefault : c.resolve;
 }
 
 Layout make_layout(const ptebd_config& cfg) {
@@ -77,7 +94,7 @@ Layout make_layout(const ptebd_config& cfg) {
     L.off_bond_nu = o; o = align256(o + N * sizeof(double));
     L.off_bond_rank = o; o = align256(o + N * sizeof(int32_t));
     L.off_bond_sweeps = o; o = align256(o + N * sizeof(int32_t));
-    L.off_totals = o; o = align256(o + 8 * sizeof(double) + 8 * sizeof(unsigned long long));
+    L.off_totals = o; o = align256(o + 8 * sizeof(double) + kWork * sizeof(unsigned long long));
     L.off_err = o; o = align256(o + sizeof(uint32_t));
     L.off_gates = o; o = align256(o + nb * 32 * sizeof(double));
     L.off_bonds = o; o = align256(o + 3 * nb * sizeof(int32_t));
@@ -86,9 +103,12 @@ Layout make_layout(const ptebd_config& cfg) {
     L.state_bytes = o;
     const size_t ldw = (size_t)L.ldw;
     L.slot_w = align256(ldw * ldw * L.elem);
-    L.slot_small = 2 * ldw * sizeof(double) + ldw * sizeof(int32_t) + 8 * sizeof(int32_t) + 2 * sizeof(double) +
-                   sizeof(int32_t);
-    L.slot_bytes = 3 * L.slot_w + L.slot_small;
+    L.slot_small = 2 * ldw * sizeof(double) + ldw * sizeof(int32_t) + kDims * sizeof(int32_t) +
+                   2 * sizeof(double) + sizeof(int32_t);
+    L.resolve = resolve_level(cfg);
+    L.resolve64 = cfg.precision == PTEBD_MIXED && L.resolve > cfg.cutoff;
+    L.slot_r = L.resolve64 ? align256(ldw * ldw * sizeof(double2)) : 0;
+    L.slot_bytes = 3 * L.slot_w + 2 * L.slot_r + L.slot_small;
     return L;
 }
 
@@ -99,7 +119,9 @@ namespace {
 // Workspace regions for `slots` slots.
 struct WsView {
     void* w; void* w0; void* w1; double* norms; double* sig; int32_t* perm; int32_t* dims;
-    double* slot_eps; double* slot_lognu; int32_t* slot_sweeps; size_t bytes;
+    double* slot_eps; double* slot_lognu; int32_t* slot_sweeps;
+    double2* r; double2* r0;  // FP64 resolution matrices (null when the config has none)
+    size_t bytes;
 };
 
 WsView ws_view(const Layout& L, char* base, int slots) {
@@ -112,10 +134,15 @@ WsView ws_view(const Layout& L, char* base, int slots) {
     v.norms = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
     v.sig = reinterpret_cast<double*>(base + o); o = align256(o + s * ldw * sizeof(double));
     v.perm = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * ldw * sizeof(int32_t));
-    v.dims = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * 8 * sizeof(int32_t));
+    v.dims = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * kDims * sizeof(int32_t));
     v.slot_eps = reinterpret_cast<double*>(base + o); o = align256(o + s * sizeof(double));
     v.slot_lognu = reinterpret_cast<double*>(base + o); o = align256(o + s * sizeof(double));
     v.slot_sweeps = reinterpret_cast<int32_t*>(base + o); o = align256(o + s * sizeof(int32_t));
+    v.r = v.r0 = nullptr;
+    if (L.slot_r) {
+        v.r = reinterpret_cast<double2*>(base + o); o = align256(o + s * L.slot_r);
+        v.r0 = reinterpret_cast<double2*>(base + o); o = align256(o + s * L.slot_r);
+    }
     v.bytes = o;
     return v;
 }
@@ -155,14 +182,8 @@ int validate_config(const ptebd_config* c, std::string* why) {
     }
     if (c->g < 0) { *why = "g must be >= 0"; return PTEBD_ERR_INVALID; }
     if (!(c->cutoff >= 0.0) || !std::isfinite(c->cutoff)) { *why = "cutoff must be finite and >= 0"; return PTEBD_ERR_INVALID; }
-    if (std::isnan(c->floor)) { *why = "floor is NaN"; return PTEBD_ERR_INVALID; }
+    if (std::isnan(c->resolve) || std::isinf(c->resolve)) { *why = "resolve must be finite"; return PTEBD_ERR_INVALID; }
     return PTEBD_OK;
-}
-
-double effective_threshold(const ptebd_config& c) {
-    double fl = 0.0;
-    if (c.precision == PTEBD_MIXED) fl = c.floor < 0.0 ? 1e-6 : c.floor;
-    return std::max(c.cutoff, fl);
 }
 
 template <typename T> T* at(char* base, size_t off) { return reinterpret_cast<T*>(base + off); }
@@ -270,7 +291,7 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     char* m = st->mem;
     WsView ws = ws_view(L, st->ws, st->slots);
     LayerArgs<R> a{};
-    a.gamma = at<cx_t<R>>(m, L.off_gamma);
+    a.gamma = m + L.off_gamma;
     a.lam = at<double>(m, L.off_lam);
     a.chi = at<int32_t>(m, L.off_chi);
     a.w = reinterpret_cast<cx_t<R>*>(ws.w);
@@ -281,7 +302,9 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     a.norms = ws.norms; a.sig = ws.sig; a.perm = ws.perm; a.dims = ws.dims;
     a.slot_eps = ws.slot_eps; a.slot_lognu = ws.slot_lognu; a.slot_sweeps = ws.slot_sweeps;
     a.chip = L.chip; a.ldw = L.ldw; a.n_sites = L.n_sites; a.chi_max = L.chi_max;
-    a.thr_rel = effective_threshold(st->cfg);
+    a.thr_rel = st->cfg.cutoff;
+    a.resolve = L.resolve64 ? L.resolve : 0.0;
+    a.refine = 0;
     a.eps_mode = st->cfg.eps_mode;
     a.stabilise = gated ? 1 : 0;
     a.max_sweeps = 40;
@@ -302,32 +325,81 @@ void at_slots(LayerArgs<R>& a, const Layout& L, int base) {
     const size_t ldw = (size_t)L.ldw, b = (size_t)base;
     const size_t per_w = L.slot_w / sizeof(cx_t<R>);
     a.w += b * per_w; a.w0 += b * per_w; a.w1 += b * per_w;
-    a.norms += b * ldw; a.sig += b * ldw; a.perm += b * ldw; a.dims += b * 8;
+    a.norms += b * ldw; a.sig += b * ldw; a.perm += b * ldw; a.dims += b * kDims;
     a.slot_eps += b; a.slot_lognu += b; a.slot_sweeps += b;
 }
 
-// The kernel chain of one stage on a.count bonds (slots and bonds already set),
-// on stream s; `wrap(kind, launch)` brackets each launch (timing or not).
-template <typename R, typename W>
-int launch_chain(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&& wrap) {
+// Arguments of the FP64 resolution pass over the same slots (and bonds, gates,
+// counts) as the complex64 pass `c`: FP64 matrices in the r / r0 regions (slot j
+// at j ldw^2 complex128 elements, as the kernels index them), the small per-slot
+// arrays shared with the complex64 pass (dead for an undecided bond, untouched
+// for the others), the cutoff alone as threshold.  For tSU the X factor takes
+// the first chip columns of r and M^dag the last chip columns.
+LayerArgs<double> refine_args(ptebd_state* st, const LayerArgs<float>& c, int base) {
+    const Layout& L = st->L;
+    WsView ws = ws_view(L, st->ws, st->slots);
+    LayerArgs<double> a{};
+    a.gamma = c.gamma; a.lam = c.lam; a.chi = c.chi;
+    const size_t per = (size_t)L.ldw * L.ldw, b = (size_t)base;
+    a.w = ws.r + b * per;
+    a.w0 = ws.r0 + b * per;
+    a.w1 = a.w + (size_t)L.chip * L.ldw;
+    a.norms = c.norms; a.sig = c.sig; a.perm = c.perm; a.dims = c.dims;
+    a.slot_eps = c.slot_eps; a.slot_lognu = c.slot_lognu; a.slot_sweeps = c.slot_sweeps;
+    a.bonds = c.bonds; a.gates = c.gates;
+    a.count = c.count; a.chip = c.chip; a.ldw = c.ldw; a.n_sites = c.n_sites; a.chi_max = c.chi_max;
+    a.thr_rel = st->cfg.cutoff;
+    a.resolve = 0.0;
+    a.refine = 1;
+    a.eps_mode = c.eps_mode; a.stabilise = c.stabilise; a.max_sweeps = c.max_sweeps; a.wait_test = 0;
+    a.mode = c.mode; a.pass = 0;
+    a.bond_eps = c.bond_eps; a.bond_nu = c.bond_nu; a.bond_rank = c.bond_rank; a.bond_sweeps = c.bond_sweeps;
+    a.totals = c.totals; a.err = c.err; a.work = c.work;
+    return a;
+}
+
+// The kernels of one stage on a.count bonds (slots and bonds already set), on
+// stream s, Gamma stored as G; `wrap(kind, launch)` brackets each launch.  With
+// a.refine every kernel runs only the bonds the complex64 pass left undecided.
+template <typename R, typename G, typename W>
+int launch_pass(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&& wrap) {
+    const int kt = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_THETA, ks = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_SVD,
+              kc = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_TRUNCATE, kg = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_GAMMA,
+              kf = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_FACTOR;
     if (gated) {
-        CUDA_TRY(st, wrap(PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(a, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(a, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_GAMMA, [&] { return launch_gamma<R>(a, s); }));
+        CUDA_TRY(st, wrap(kt, [&] { return launch_theta<R, G>(a, s); }));
+        CUDA_TRY(st, wrap(ks, [&] { return launch_jacobi<R>(a, s); }));
+        CUDA_TRY(st, wrap(kc, [&] { return launch_truncate<R>(a, s); }));
+        CUDA_TRY(st, wrap(kg, [&] { return launch_gamma<R, G>(a, s); }));
     } else {
         // tSU: SVD of theta = X Y through its rank-chi_b factors
         LayerArgs<R> x = a;
         x.pass = 1;
         LayerArgs<R> y = a;
         y.w = a.w1;
-        CUDA_TRY(st, wrap(PTEBD_K_THETA, [&] { return launch_theta<R>(a, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_xform<R>(x, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_orth<R>(x, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_FACTOR, [&] { return launch_proj<R>(x, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_SVD, [&] { return launch_jacobi<R>(y, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_TRUNCATE, [&] { return launch_truncate<R>(y, s); }));
-        CUDA_TRY(st, wrap(PTEBD_K_GAMMA, [&] { return launch_gamma<R>(y, s); }));
+        CUDA_TRY(st, wrap(kt, [&] { return launch_theta<R, G>(a, s); }));
+        CUDA_TRY(st, wrap(kf, [&] { return launch_xform<R, G>(x, s); }));
+        CUDA_TRY(st, wrap(kf, [&] { return launch_orth<R>(x, s); }));
+        CUDA_TRY(st, wrap(kf, [&] { return launch_proj<R>(x, s); }));
+        CUDA_TRY(st, wrap(ks, [&] { return launch_jacobi<R>(y, s); }));
+        CUDA_TRY(st, wrap(kc, [&] { return launch_truncate<R>(y, s); }));
+        CUDA_TRY(st, wrap(kg, [&] { return launch_gamma<R, G>(y, s); }));
+    }
+    return PTEBD_OK;
+}
+
+// The kernel chain of one stage on a.count bonds starting at workspace slot
+// `base` (a already points there), on stream s; for a complex64 state with FP64
+// resolution the FP64 pass over the undecided bonds follows, then the sums.
+template <typename R, typename W>
+int launch_chain(ptebd_state* st, LayerArgs<R> a, int base, bool gated, cudaStream_t s, W&& wrap) {
+    int rc = launch_pass<R, cx_t<R>>(st, a, gated, s, wrap);
+    if (rc) return rc;
+    if constexpr (std::is_same<R, float>::value) {
+        if (st->L.resolve64) {
+            rc = launch_pass<double, float2>(st, refine_args(st, a, base), gated, s, wrap);
+            if (rc) return rc;
+        }
     }
     CUDA_TRY(st, wrap(PTEBD_K_REDUCE, [&] {
                  return launch_reduce_layer(a.slot_eps, a.slot_lognu, a.count, gated ? 1 : 0, a.totals, s);
@@ -344,7 +416,7 @@ int run_stage_serial(ptebd_state* st, const Stage& g) {
         a.count = std::min(st->slots, g.nb - c0);
         a.bonds = g.d_list + c0;
         a.gates = g.gated ? g.d_gates + (size_t)c0 * 32 : nullptr;
-        int rc = launch_chain<R>(st, a, g.gated, st->stream, wrap);
+        int rc = launch_chain<R>(st, a, 0, g.gated, st->stream, wrap);
         if (rc) return rc;
     }
     return PTEBD_OK;
@@ -400,7 +472,7 @@ int run_stages_chunked(ptebd_state* st, const std::vector<Stage>& stages, const 
             a.bonds = g.d_list + off[c];
             a.gates = g.gated ? g.d_gates + (size_t)off[c] * 32 : nullptr;
             a.totals = part + 4 * c;
-            rc = launch_chain<R>(st, a, g.gated, st->aux[c], wrap);
+            rc = launch_chain<R>(st, a, c * p.cap, g.gated, st->aux[c], wrap);
             if (rc) return rc;
             CUDA_TRY(st, cudaEventRecord(st->chunk_ev[c], st->aux[c]));
             recorded[c] = true;
@@ -420,7 +492,13 @@ struct NvtxRange {
 };
 
 // A gated stage (or none) followed by g PtSU steps.
+int refuse_poisoned(ptebd_state* st) {
+    return set_err(st, PTEBD_ERR_TIMEOUT, "the state is unusable after an earlier device wait ran out with copies "
+                                          "in flight: destroy and re-create it");
+}
+
 int run_layer(ptebd_state* st, const Stage* gated_stage, int g) {
+    if (st->poisoned) return refuse_poisoned(st);
     NvtxRange range(gated_stage ? (g ? "ptebd layer + PtSU" : "ptebd layer") : "ptebd PtSU");
     const Layout& L = st->L;
     const int32_t* lists = at<int32_t>(st->mem, L.off_bonds);
@@ -463,6 +541,13 @@ int check_device_errors(ptebd_state* st) {
     if (!err) return PTEBD_OK;
     CUDA_TRY(st, cudaMemsetAsync(d_err, 0, sizeof(uint32_t), st->stream));
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+    if (err & DERR_DRAIN) {
+        st->poisoned = true;
+        return set_err(st, PTEBD_ERR_TIMEOUT,
+                       "a bounded device wait ran out and a CTA returned with bulk copies in flight (0x%x): "
+                       "destroy and re-create the state",
+                       err);
+    }
     if (err & DERR_BADARG)
         return set_err(st, PTEBD_ERR_INVALID, "a bond or bond dimension out of range reached the device (0x%x)", err);
     if (err & DERR_TIMEOUT) return set_err(st, PTEBD_ERR_TIMEOUT, "a bounded device wait ran out (0x%x)", err);
@@ -474,6 +559,7 @@ int check_device_errors(ptebd_state* st) {
 }
 
 int sync_and_check(ptebd_state* st) {
+    if (st->poisoned) return refuse_poisoned(st);
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
     return check_device_errors(st);
 }
@@ -738,6 +824,8 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
     cudaGetDevice(&st->device);
     cudaError_t e = cfg->precision == PTEBD_FP64 ? jacobi_prepare<double>() : jacobi_prepare<float>();
     if (e == cudaSuccess) e = cfg->precision == PTEBD_FP64 ? orth_prepare<double>() : orth_prepare<float>();
+    if (e == cudaSuccess && L.resolve64) e = jacobi_prepare<double>();
+    if (e == cudaSuccess && L.resolve64) e = orth_prepare<double>();
     if (e != cudaSuccess) {
         delete st;
         return PTEBD_ERR_CUDA;
@@ -778,6 +866,7 @@ int ptebd_set_stream(ptebd_state* st, void* stream) {
 
 int ptebd_reset(ptebd_state* st) {
     if (!st) return PTEBD_ERR_INVALID;
+    if (st->poisoned) return refuse_poisoned(st);
     CUDA_TRY(st, cudaMemsetAsync(st->mem, 0, st->L.state_bytes, st->stream));
     k_init_state<<<64, 256, 0, st->stream>>>(st->mem, st->L);
     CUDA_TRY(st, cudaGetLastError());
@@ -1021,11 +1110,11 @@ int ptebd_bond_stats(ptebd_state* st, double* eps, double* nu, int32_t* rank_in)
 
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n) {
     if (!st || !out || n < 0) return PTEBD_ERR_INVALID;
-    unsigned long long w[8];
+    unsigned long long w[kWork];
     CUDA_TRY(st, cudaMemcpyAsync(w, at<double>(st->mem, st->L.off_totals) + 8, sizeof w, cudaMemcpyDeviceToHost,
                                  st->stream));
     CUDA_TRY(st, cudaStreamSynchronize(st->stream));
-    for (int i = 0; i < std::min(n, 8); ++i) out[i] = w[i];
+    for (int i = 0; i < std::min(n, kWork); ++i) out[i] = w[i];
     return PTEBD_OK;
 }
 

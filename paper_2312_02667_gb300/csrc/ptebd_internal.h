@@ -19,6 +19,11 @@ template <typename R> using cx_t = typename Cx<R>::T;
 template <typename C> __host__ __device__ __forceinline__ C cmake(double re, double im) {
     C c; c.x = (decltype(c.x))re; c.y = (decltype(c.y))im; return c;
 }
+// complex conversion between storage and arithmetic types (exact from float2 to
+// double2, rounded to nearest the other way)
+template <typename T, typename F> __host__ __device__ __forceinline__ T cconv(F v) {
+    T c; c.x = (decltype(c.x))v.x; c.y = (decltype(c.y))v.y; return c;
+}
 
 // --------------------------------------------------------- device errors --
 // Bits of the latched device error word.
@@ -29,6 +34,8 @@ enum : uint32_t {
     DERR_NOT_CONVERGED = 8u, // a Jacobi SVD hit its sweep limit
     DERR_TIMEOUT = 16u,      // a bounded wait on an mbarrier ran out
     DERR_BADARG = 32u,       // a bond or bond dimension out of range reached a kernel (skipped)
+    DERR_DRAIN = 64u,        // after a wait ran out, a CTA's own bulk copies did not finish either: the CTA
+                             // returned with copies into its shared memory possibly still in flight
 };
 
 // ------------------------------------------------------------- layout ----
@@ -52,7 +59,10 @@ enum : uint32_t {
 //   w, w0, w1 : ldw x ldw complex each (ldw = 2 chip); w is rotated by the SVD,
 //            w0 keeps theta' (or its adjoint) for the second factor, w1 holds
 //            the second matrix of the tSU factorisation
-//   norms, sig : ldw doubles; perm : ldw int32; dims : 8 int32
+//   norms, sig : ldw doubles; perm : ldw int32; dims : kDims int32
+//   (PTEBD_MIXED with FP64 resolution) r, r0 : ldw x ldw complex128 each, the
+//            FP64 recomputation of a gated bond whose truncation the complex64
+//            spectrum leaves undecided
 struct Layout {
     int n_sites = 0, chi_max = 0, chip = 0, ldw = 0, precision = 0, max_bonds = 0;
     size_t elem = 0;  // bytes of one complex element of gamma / w
@@ -60,8 +70,11 @@ struct Layout {
     size_t off_gamma = 0, off_lam = 0, off_chi = 0, off_bond_eps = 0, off_bond_nu = 0,
            off_bond_rank = 0, off_bond_sweeps = 0, off_totals = 0, off_err = 0,
            off_gates = 0, off_bonds = 0, off_scratch = 0, off_partials = 0, state_bytes = 0;
-    // per-slot workspace (bytes)
-    size_t slot_w = 0, slot_small = 0, slot_bytes = 0;
+    // per-slot workspace (bytes); slot_r: one complex128 matrix of the FP64
+    // resolution (0 when the config does not use it)
+    size_t slot_w = 0, slot_small = 0, slot_r = 0, slot_bytes = 0;
+    bool resolve64 = false;  // PTEBD_MIXED bonds undecided in complex64 are recomputed in FP64
+    double resolve = 0.0;    // the relative level below which complex64 singular values are not trusted
 };
 
 Layout make_layout(const ptebd_config& cfg);
@@ -70,12 +83,18 @@ Layout make_layout(const ptebd_config& cfg);
 template <typename R>
 struct LayerArgs {
     using C = cx_t<R>;
-    C* gamma; double* lam; int32_t* chi;
+    void* gamma;  // Gamma store: complex of the state's precision (float2 or double2), which may
+                  // differ from R in the FP64 resolution of a complex64 state
+    double* lam; int32_t* chi;
     C* w; C* w0; C* w1; double* norms; double* sig; int32_t* perm; int32_t* dims;
     double* slot_eps; double* slot_lognu; int32_t* slot_sweeps;
     const int32_t* bonds; const double* gates;  // gates == nullptr: tSU
     int count, chip, ldw, n_sites, chi_max;
-    double thr_rel;   // relative threshold max(cutoff, floor)
+    double thr_rel;   // relative truncation threshold: the cutoff, or max(cutoff, resolve) when the
+                      // complex64 spectrum decides a bond without the FP64 resolution
+    double resolve;   // > thr_rel: bonds whose kept count depends on singular values <= resolve * sigma_1
+                      // are left undecided (dims D_REFINE = 1) for the FP64 resolution; 0: off
+    int refine;       // 1: this launch is the FP64 resolution pass (only bonds with D_REFINE = 1 run)
     int eps_mode, stabilise, max_sweeps;
     int wait_test;    // test of the bounded waits: one hand-off wait per CTA targets a count nothing
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
@@ -84,18 +103,23 @@ struct LayerArgs {
     double* bond_eps; double* bond_nu; int32_t* bond_rank; int32_t* bond_sweeps;
     double* totals; uint32_t* err;
     unsigned long long* work;  // [0] Jacobi pair-row visits, [1] theta flops, [2] rotations,
-                               // [3] sweeps summed, [4] SVDs
+                               // [3] sweeps summed, [4] SVDs; [5..7] the same for tSU;
+                               // [8] bonds recomputed in FP64, [9] their Jacobi visits
 };
 
-// dims[] entries of a slot
-enum { D_CL = 0, D_CM = 1, D_CR = 2, D_TALL = 3, D_BOND = 4, D_K = 5, D_ROWS = 6, D_COLS = 7 };
+// dims[] entries of a slot (kDims int32 per slot)
+enum { D_CL = 0, D_CM = 1, D_CR = 2, D_TALL = 3, D_BOND = 4, D_K = 5, D_ROWS = 6, D_COLS = 7,
+       D_REFINE = 8 };
+constexpr int kDims = 16;
+constexpr int kWork = 16;  // work counters
 
 // ------------------------------------------------------------ launchers --
-template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s);
+// G: the complex type of the Gamma store (cx_t<R> except in the FP64 resolution)
+template <typename R, typename G = cx_t<R>> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s);
-template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
-template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R, typename G = cx_t<R>> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
+template <typename R, typename G = cx_t<R>> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s);
 // pass 1 of the tSU SVD: an orthonormal basis of the columns of X (ptebd_orth.cu)
 template <typename R> cudaError_t launch_orth(const LayerArgs<R>& a, cudaStream_t s);

@@ -505,11 +505,15 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     auto abort_drain = [&]() {
         // Called by all threads after a wait ran out: wait (bounded) once more
         // for the loads still in flight, drain our bulk stores, latch the error.
+        // If a load still has not landed, the CTA has to return with it in flight
+        // (nothing can cancel a bulk copy, and waiting on would hang the GPU):
+        // DERR_DRAIN marks the state unusable until it is re-created.
         if (tid == 0) {
+            bool drained = true;
             for (int b = 0; b < 2; ++b)
-                if (sh[3 + b]) mbar_wait_bounded(&bar[b], (uint32_t)sh[5 + b]);
+                if (sh[3 + b] && !mbar_wait_bounded(&bar[b], (uint32_t)sh[5 + b])) drained = false;
             bulk_wait_all();
-            atomicOr(A.err, DERR_TIMEOUT);
+            atomicOr(A.err, drained ? DERR_TIMEOUT : (DERR_TIMEOUT | DERR_DRAIN));
         }
         __syncthreads();
     };
@@ -730,7 +734,12 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     if (tid == 0) { bulk_wait_all(); fence_async_global(); }
     __syncthreads();
     if (!converged && tid == 0) atomicOr(A.err, DERR_NOT_CONVERGED);
-    if (tid == 0) {
+    if (tid == 0 && A.refine) {  // the FP64 resolution of a complex64 state, counted apart
+        A.slot_sweeps[j] = sweep;
+        atomicAdd(&A.work[8], 1ull);
+        atomicAdd(&A.work[9], (unsigned long long)sweep * (unsigned long long)(cols * (cols - 1) / 2) *
+                                  (unsigned long long)rows);
+    } else if (tid == 0) {
         A.slot_sweeps[j] = sweep;
         atomicAdd(&A.work[0], (unsigned long long)sweep * (unsigned long long)(cols * (cols - 1) / 2) *
                                   (unsigned long long)rows);
@@ -786,7 +795,8 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     using C = cx_t<R>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int j = blockIdx.x;
-    const int32_t* d = A.dims + j * 8;
+    const int32_t* d = A.dims + j * kDims;
+    if (A.refine && d[D_REFINE] != 1) return;  // the FP64 resolution runs only undecided bonds
     const int rows = A.pass == 1 ? 2 * d[D_CL] : d[D_ROWS];
     const int cols = A.pass == 1 ? d[D_CM] : d[D_COLS];
     C* W = A.w + (size_t)j * A.ldw * A.ldw;

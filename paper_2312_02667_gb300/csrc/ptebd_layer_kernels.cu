@@ -43,10 +43,15 @@ template <typename C> __device__ __forceinline__ void cfma_cj(C& acc, C x, C y) 
 // X_s = diag(Lambda_{b-1}) Gamma_b^s diag(Lambda_b), Y_t = Gamma_{b+1}^t diag(Lambda_{b+1}),
 // mixes them with the gate and writes theta' (tall: rows (s,alpha), cols (t,gamma))
 // or its adjoint (wide) into w and w0.
-template <typename R>
+// G: the complex type of the Gamma store, read as is and widened to C (the FP64
+// resolution of a complex64 state forms theta' in FP64 from complex64 Gamma).
+// In the resolution pass (a.refine) only bonds marked undecided run, and their
+// dims (written by the first pass, unchanged since) are left alone.
+template <typename R, typename G>
 __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z;
+    if (a.refine && a.dims[j * kDims + D_REFINE] != 1) return;
     const int b = a.bonds[j];
     const int chip = a.chip;
     // device-side argument check: a bond or dimension out of range (a corrupted
@@ -54,9 +59,9 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     // rows and columns make the SVD, truncation and Gamma kernels do nothing
     if (b < 0 || b > a.n_sites - 2 || a.chi[b] < 1 || a.chi[b] > chip || a.chi[b + 1] < 1 ||
         a.chi[b + 1] > chip || a.chi[b + 2] < 1 || a.chi[b + 2] > chip) {
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-            int32_t* d = a.dims + j * 8;
-            for (int q = 0; q < 8; ++q) d[q] = 0;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !a.refine) {
+            int32_t* d = a.dims + j * kDims;
+            for (int q = 0; q < kDims; ++q) d[q] = 0;
             d[D_TALL] = 1;
             atomicOr(a.err, DERR_BADARG);
         }
@@ -65,10 +70,11 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
     // tSU (mode 1) always stores theta^dag: its SVD goes through the factors
     const bool tall = a.mode == 0 && cl >= cr;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        int32_t* d = a.dims + j * 8;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !a.refine) {
+        int32_t* d = a.dims + j * kDims;
         d[D_CL] = cl; d[D_CM] = cm; d[D_CR] = cr; d[D_TALL] = tall ? 1 : 0; d[D_BOND] = b;
         d[D_K] = 0;
+        d[D_REFINE] = 0;
         if (a.mode == 0) { d[D_ROWS] = tall ? 2 * cl : 2 * cr; d[D_COLS] = tall ? 2 * cr : 2 * cl; }
         else { d[D_ROWS] = 2 * cr; d[D_COLS] = cm; }
         atomicAdd(&a.work[1], 32ull * (unsigned long long)cl * (unsigned long long)cm * (unsigned long long)cr);
@@ -83,8 +89,8 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     __shared__ R sL[32], sR[32], sM[PTEBD_CHI_LIMIT];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const size_t slice = (size_t)chip * chip;
-    const C* G0 = a.gamma + (size_t)b * 2 * slice;
-    const C* G1 = a.gamma + (size_t)(b + 1) * 2 * slice;
+    const G* G0 = static_cast<const G*>(a.gamma) + (size_t)b * 2 * slice;
+    const G* G1 = static_cast<const G*>(a.gamma) + (size_t)(b + 1) * 2 * slice;
     {
         const double* lL = a.lam + (size_t)b * chip;
         const double* lM = a.lam + (size_t)(b + 1) * chip;
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
             const int alpha = a0 + al, beta = k0 + kk;
             C v = cz<C>();
             if (alpha < cl && beta < cm)
-                v = cscale(G0[s * slice + (size_t)beta * chip + alpha], sL[al] * sM[beta]);
+                v = cscale(cconv<C>(G0[s * slice + (size_t)beta * chip + alpha]), sL[al] * sM[beta]);
             xs[s][kk][al] = v;
         }
         for (int e = threadIdx.x; e < 1024; e += 256) {
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
             const int gamma = g0 + gg, beta = k0 + kk;
             C v = cz<C>();
             if (gamma < cr && beta < cm)
-                v = cscale(G1[t * slice + (size_t)gamma * chip + beta], sR[gg]);
+                v = cscale(cconv<C>(G1[t * slice + (size_t)gamma * chip + beta]), sR[gg]);
             ys[t][kk][gg] = v;
         }
         __syncthreads();
@@ -193,17 +199,83 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
 }
 
 // ------------------------------------------------------------- truncate --
+// Operator Schmidt rank of a two-site gate, U = sum_k A_k (x) B_k with A_k on the
+// left site and B_k on the right: the rank of the rearranged matrix
+// R[(s', s), (t', t)] = U[(2 s' + t'), (2 s + t)].  theta' is a sum of rank(R)
+// terms (A_k (x) 1) theta (B_k (x) 1)^T of rank <= chi_b each, so
+// rank(theta') <= rank(R) chi_b.  One thread: a one-sided Jacobi on the four
+// columns of R in FP64 (gates are given in FP64), rank = #{s_k > 1e-12 s_1}.
+__device__ int op_schmidt_rank(const double* g) {
+    double re[4][4], im[4][4];  // [column (t', t)][row (s', s)]
+    for (int sp = 0; sp < 2; ++sp)
+        for (int s0 = 0; s0 < 2; ++s0)
+            for (int tp = 0; tp < 2; ++tp)
+                for (int t0 = 0; t0 < 2; ++t0) {
+                    const int e = (2 * sp + tp) * 4 + (2 * s0 + t0);
+                    re[2 * tp + t0][2 * sp + s0] = g[2 * e];
+                    im[2 * tp + t0][2 * sp + s0] = g[2 * e + 1];
+                }
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                double al = 0, be = 0, gr = 0, gi = 0;  // |c_p|^2, |c_q|^2, c_p^H c_q
+                for (int r = 0; r < 4; ++r) {
+                    al += re[p][r] * re[p][r] + im[p][r] * im[p][r];
+                    be += re[q][r] * re[q][r] + im[q][r] * im[q][r];
+                    gr += re[p][r] * re[q][r] + im[p][r] * im[q][r];
+                    gi += re[p][r] * im[q][r] - im[p][r] * re[q][r];
+                }
+                const double g2 = gr * gr + gi * gi;
+                if (!(g2 > 1e-30 * al * be)) continue;
+                rotated = true;
+                const double gm = sqrt(g2), er = gr / gm, ei = gi / gm;
+                const double zeta = (be - al) / (2.0 * gm);
+                double t = 1.0 / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                if (zeta < 0) t = -t;
+                const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                // c_p' = c c_p - sn conj(e) c_q,  c_q' = c c_q + sn e c_p
+                for (int r = 0; r < 4; ++r) {
+                    const double pr = re[p][r], pi = im[p][r], qr = re[q][r], qi = im[q][r];
+                    re[p][r] = c * pr - sn * (er * qr + ei * qi);
+                    im[p][r] = c * pi - sn * (er * qi - ei * qr);
+                    re[q][r] = c * qr + sn * (er * pr - ei * pi);
+                    im[q][r] = c * qi + sn * (er * pi + ei * pr);
+                }
+            }
+        if (!rotated) break;
+    }
+    double nrm[4], mx = 0;
+    for (int p = 0; p < 4; ++p) {
+        double s2 = 0;
+        for (int r = 0; r < 4; ++r) s2 += re[p][r] * re[p][r] + im[p][r] * im[p][r];
+        nrm[p] = sqrt(s2);
+        mx = fmax(mx, nrm[p]);
+    }
+    int rank = 0;
+    for (int p = 0; p < 4; ++p) rank += nrm[p] > 1e-12 * mx ? 1 : 0;
+    return rank;
+}
+
 // grid (count), 512 threads.  norms[] holds the FP64 column norms of the
 // rotated matrix (= the singular values, unsorted).
+// With a.resolve > a.thr_rel (the complex64 pass of a state with FP64
+// resolution), singular values <= resolve * sigma_1 are not trusted: the kept
+// count is decided only if it is the same whether they are taken as real or as
+// zero, that is k_hi = min(chi_max, r_max, #{S > resolve S_1}) equals
+// k_lo = min(chi_max, r_max, #{S > thr S_1}), with r_max = min(cols,
+// rank(gate) chi_b) the structural bound on rank(theta').  An undecided bond is
+// marked (dims D_REFINE = 1) and left alone: the FP64 pass recomputes it.
 template <typename R>
 __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
     constexpr int NS = 512;
     __shared__ double key[NS];
     __shared__ int idx[NS];
     __shared__ double red[NS];
-    __shared__ int kept_sh;
+    __shared__ int kept_sh, kept_hi_sh, rmax_sh;
     const int j = blockIdx.x, t = threadIdx.x;
-    int32_t* d = a.dims + j * 8;
+    int32_t* d = a.dims + j * kDims;
+    if (a.refine && d[D_REFINE] != 1) return;
     const int ncols = d[D_COLS];
     const int b = d[D_BOND];
     const double* nrm = a.norms + (size_t)j * a.ldw;
@@ -235,12 +307,40 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
         return;
     }
     const double thr = a.thr_rel * smax;
-    // number above the threshold (the keys are sorted)
-    if (t == 0) kept_sh = 0;
+    const bool resolving = !a.refine && a.resolve > a.thr_rel;
+    const double thr_hi = resolving ? a.resolve * smax : thr;
+    // numbers above the thresholds (the keys are sorted)
+    if (t == 0) {
+        kept_sh = 0;
+        kept_hi_sh = 0;
+    }
     __syncthreads();
     if (t < ncols && key[t] > thr && (t + 1 == ncols || !(key[t + 1] > thr))) kept_sh = t + 1;
+    if (t < ncols && key[t] > thr_hi && (t + 1 == ncols || !(key[t + 1] > thr_hi))) kept_hi_sh = t + 1;
     __syncthreads();
-    const int k = max(1, min(a.chi_max, kept_sh));
+    int k = max(1, min(a.chi_max, kept_sh));
+    if (resolving) {
+        int k_lo = min(a.chi_max, kept_sh);
+        int k_hi = min(a.chi_max, kept_hi_sh);
+        if (k_hi < k_lo && a.gates != nullptr) {
+            // undecided on the counts alone: the structural bound on rank(theta')
+            // may still decide it (taken only now, it is a few hundred cycles of one thread)
+            if (t == 0) rmax_sh = min(ncols, op_schmidt_rank(a.gates + (size_t)j * 32) * d[D_CM]);
+            __syncthreads();
+            k_lo = min(k_lo, rmax_sh);
+            k_hi = min(k_hi, rmax_sh);
+        }
+        if (k_hi < k_lo) {
+            if (t == 0) {
+                d[D_REFINE] = 1;
+                d[D_K] = 0;  // the Gamma kernels of this pass skip the bond
+                a.slot_eps[j] = 0.0;
+                a.slot_lognu[j] = 0.0;
+            }
+            return;
+        }
+        k = max(1, k_hi);
+    }
     // FP64 weights: total and dropped, fixed-order tree sums
     const double w = (t < ncols) ? key[t] * key[t] : 0.0;
     red[t] = w;
@@ -294,11 +394,12 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
 // tall (w = theta' = U S): Gamma_b[s](alpha, beta) = w[(s,alpha), perm beta] / (S_beta Lambda_{b-1,alpha})
 // wide (w = theta'^dag = V S): Gamma_{b+1}[t](beta, gamma) = conj(w[(t,gamma), perm beta]) / (S_beta Lambda_{b+1,gamma})
 // grid (ceil(chip*chip/256), 2, count), 256 threads; writes the whole padded slice.
-template <typename R>
+template <typename R, typename G>
 __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z, sg = blockIdx.y;
-    const int32_t* d = a.dims + j * 8;
+    const int32_t* d = a.dims + j * kDims;
+    if (a.refine && d[D_REFINE] != 1) return;
     const int k = d[D_K];
     if (k == 0) return;  // error latched by k_truncate
     const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND];
@@ -319,14 +420,14 @@ __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
             const double* lL = a.lam + (size_t)b * chip;
             v = cscale(W[(size_t)perm[col] * ldw + (size_t)sg * cl + row], inv_prod<R>(sig[col], lL[row]));
         }
-        a.gamma[(size_t)b * 2 * slice + sg * slice + e] = v;
+        static_cast<G*>(a.gamma)[(size_t)b * 2 * slice + sg * slice + e] = cconv<G>(v);
     } else {
         // row = beta, col = gamma
         if (row < k && col < cr) {
             const double* lR = a.lam + (size_t)(b + 2) * chip;
             v = cscale(cconj(W[(size_t)perm[row] * ldw + (size_t)sg * cr + col]), inv_prod<R>(sig[row], lR[col]));
         }
-        a.gamma[(size_t)(b + 1) * 2 * slice + sg * slice + e] = v;
+        static_cast<G*>(a.gamma)[(size_t)(b + 1) * 2 * slice + sg * slice + e] = cconv<G>(v);
     }
 }
 
@@ -339,11 +440,12 @@ __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
 // wide: P = w0 = theta'^dag, Q = w (columns perm beta) / S, Z = U S:
 //       Gamma_b[s](alpha, beta) = Z[(s,alpha), beta] / (S_beta Lambda_{b-1,alpha})
 // grid (ceil(chip/32), ceil(chip/32), 2 count), 256 threads, 2x2 outputs per thread.
-template <typename R>
+template <typename R, typename G>
 __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z >> 1, sg = blockIdx.z & 1;
-    const int32_t* d = a.dims + j * 8;
+    const int32_t* d = a.dims + j * kDims;
+    if (a.refine && d[D_REFINE] != 1) return;
     const int k = d[D_K];
     if (k == 0) return;
     const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND], rows = d[D_ROWS];
@@ -353,7 +455,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
     const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
     const int rlim = tall ? k : cl;   // valid target rows
     const int clim = tall ? cr : k;   // valid target cols
-    C* G = a.gamma + (size_t)(tall ? b + 1 : b) * 2 * slice + sg * slice;
+    G* Gm = static_cast<G*>(a.gamma) + (size_t)(tall ? b + 1 : b) * 2 * slice + sg * slice;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     if (r0 >= rlim || c0 >= clim) {
 #pragma unroll
@@ -361,7 +463,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int row = r0 + tx + 16 * i, col = c0 + ty + 16 * q;
-                if (row < chip && col < chip) G[(size_t)col * chip + row] = cz<C>();
+                if (row < chip && col < chip) Gm[(size_t)col * chip + row] = cz<G>();
             }
         return;
     }
@@ -432,7 +534,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
                 const double ln = tall ? lnb[col] : lnb[row];
                 v = cscale(acc[i][q], inv_prod<R>(sb, ln));
             }
-            G[(size_t)col * chip + row] = v;
+            Gm[(size_t)col * chip + row] = cconv<G>(v);
         }
 }
 
@@ -444,11 +546,12 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
 // (2 chi_{b+1} x chi_b) is orthogonalised: its rotated columns are V S of theta,
 // because theta = U_X M exactly.
 // k_xform writes X into w; grid (ceil(2 chip * chip / 256), count).
-template <typename R>
+template <typename R, typename G>
 __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.y;
-    const int32_t* d = a.dims + j * 8;
+    const int32_t* d = a.dims + j * kDims;
+    if (a.refine && d[D_REFINE] != 1) return;
     const int cl = d[D_CL], cm = d[D_CM], b = d[D_BOND];
     const int chip = a.chip;
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
@@ -457,7 +560,7 @@ __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     if (beta >= cm || r >= rows) return;
     const int s = r / cl, alpha = r - s * cl;
     const size_t slice = (size_t)chip * chip;
-    const C g = a.gamma[(size_t)b * 2 * slice + s * slice + (size_t)beta * chip + alpha];
+    const C g = cconv<C>(static_cast<const G*>(a.gamma)[(size_t)b * 2 * slice + s * slice + (size_t)beta * chip + alpha]);
     const R sc = (R)a.lam[(size_t)b * chip + alpha] * (R)a.lam[(size_t)(b + 1) * chip + beta];
     a.w[(size_t)j * a.ldw * a.ldw + (size_t)beta * a.ldw + r] = cscale(g, sc);
 }
@@ -470,7 +573,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z;
-    const int32_t* d = a.dims + j * 8;
+    const int32_t* d = a.dims + j * kDims;
+    if (a.refine && d[D_REFINE] != 1) return;
     const int cl = d[D_CL], cm = d[D_CM], cr = d[D_CR];
     const int rows = 2 * cr, kdim = 2 * cl;
     const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
@@ -553,31 +657,31 @@ __global__ void k_add_partials(const double* partials, int k, double* totals) {
 }
 
 // -------------------------------------------------------------- launchers --
-template <typename R> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
+template <typename R, typename G> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
     const int tiles = (a.chip + 31) / 32;
     dim3 grid(tiles, tiles, a.count);
-    k_theta<R><<<grid, 256, 0, s>>>(a);
+    k_theta<R, G><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s) {
     k_truncate<R><<<a.count, 512, 0, s>>>(a);
     return cudaGetLastError();
 }
-template <typename R> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s) {
+template <typename R, typename G> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s) {
     const size_t slice = (size_t)a.chip * a.chip;
     dim3 g1((unsigned)((slice + 255) / 256), 2, a.count);
-    k_gamma_direct<R><<<g1, 256, 0, s>>>(a);
+    k_gamma_direct<R, G><<<g1, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int tiles = (a.chip + 31) / 32;
     dim3 g2(tiles, tiles, 2 * a.count);
-    k_gamma_gemm<R><<<g2, 256, 0, s>>>(a);
+    k_gamma_gemm<R, G><<<g2, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-template <typename R> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s) {
+template <typename R, typename G> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s) {
     const size_t n = (size_t)2 * a.chip * a.chip;
     dim3 grid((unsigned)((n + 255) / 256), a.count);
-    k_xform<R><<<grid, 256, 0, s>>>(a);
+    k_xform<R, G><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
@@ -596,14 +700,17 @@ cudaError_t launch_add_partials(const double* partials, int k, double* totals, c
     return cudaGetLastError();
 }
 
-template cudaError_t launch_theta<float>(const LayerArgs<float>&, cudaStream_t);
-template cudaError_t launch_theta<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_theta<float, float2>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_theta<double, double2>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_theta<double, float2>(const LayerArgs<double>&, cudaStream_t);
 template cudaError_t launch_truncate<float>(const LayerArgs<float>&, cudaStream_t);
 template cudaError_t launch_truncate<double>(const LayerArgs<double>&, cudaStream_t);
-template cudaError_t launch_gamma<float>(const LayerArgs<float>&, cudaStream_t);
-template cudaError_t launch_gamma<double>(const LayerArgs<double>&, cudaStream_t);
-template cudaError_t launch_xform<float>(const LayerArgs<float>&, cudaStream_t);
-template cudaError_t launch_xform<double>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_gamma<float, float2>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_gamma<double, double2>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_gamma<double, float2>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_xform<float, float2>(const LayerArgs<float>&, cudaStream_t);
+template cudaError_t launch_xform<double, double2>(const LayerArgs<double>&, cudaStream_t);
+template cudaError_t launch_xform<double, float2>(const LayerArgs<double>&, cudaStream_t);
 template cudaError_t launch_proj<float>(const LayerArgs<float>&, cudaStream_t);
 template cudaError_t launch_proj<double>(const LayerArgs<double>&, cudaStream_t);
 

@@ -33,9 +33,9 @@ SvdWs svd_ws(char* base, int precision, int batch, int rows) {
     size_t o = 0;
     v.w = base + o; o = align256(o + b * ldw * ldw * elem);
     v.norms = reinterpret_cast<double*>(base + o); o = align256(o + b * ldw * sizeof(double));
-    v.dims = reinterpret_cast<int32_t*>(base + o); o = align256(o + b * 8 * sizeof(int32_t));
+    v.dims = reinterpret_cast<int32_t*>(base + o); o = align256(o + b * kDims * sizeof(int32_t));
     v.sweeps = reinterpret_cast<int32_t*>(base + o); o = align256(o + b * sizeof(int32_t));
-    v.work = reinterpret_cast<unsigned long long*>(base + o); o = align256(o + 8 * sizeof(unsigned long long));
+    v.work = reinterpret_cast<unsigned long long*>(base + o); o = align256(o + kWork * sizeof(unsigned long long));
     v.err = reinterpret_cast<uint32_t*>(base + o); o = align256(o + sizeof(uint32_t));
     v.bytes = o;
     return v;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256) k_svd_load(const cx_t<R>* a, int lda, int
     const int j = blockIdx.y;
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
     if (e == 0) {
-        int32_t* d = dims + j * 8;
+        int32_t* d = dims + j * kDims;
         d[D_CL] = 0; d[D_CM] = 0; d[D_CR] = 0; d[D_TALL] = 1; d[D_BOND] = 0; d[D_K] = 0;
         d[D_ROWS] = rows; d[D_COLS] = cols;
     }
@@ -106,7 +106,7 @@ int run_svd(int batch, int rows, int cols, const void* a, int lda, double* sigma
     SvdWs ws = svd_ws(wsbase, precision, batch, rows);
     const int ldw = ldw_for(rows);
     if (jacobi_prepare<R>() != cudaSuccess) return PTEBD_ERR_CUDA;
-    if (cudaMemsetAsync(ws.work, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) return PTEBD_ERR_CUDA;
+    if (cudaMemsetAsync(ws.work, 0, kWork * sizeof(unsigned long long), s) != cudaSuccess) return PTEBD_ERR_CUDA;
     if (cudaMemsetAsync(ws.err, 0, sizeof(uint32_t), s) != cudaSuccess) return PTEBD_ERR_CUDA;
     dim3 g1((unsigned)(((size_t)rows * cols + 255) / 256), batch);
     k_svd_load<R><<<g1, 256, 0, s>>>(static_cast<const C*>(a), lda, rows, cols, static_cast<C*>(ws.w), ldw,

@@ -9,18 +9,22 @@
 // error word) in one file-scope device array of fixed size, so the caller
 // passes only the inputs and the outputs.
 //
-// The array is a static __device__ object: every GPU that loads the library
-// holds PTEBD_NOALLOC_SCRATCH_BYTES of it until the process exits.  Host code
-// cannot use the array's name as a device address, so the first call on each
-// device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; make that first call before any stream capture.
+// The array is a static __device__ object of this file's module.  The module
+// is loaded on a device, and the array reserved there, on first use (the CUDA
+// runtime loads modules lazily by default): the first call on each device may
+// therefore fail with PTEBD_ERR_CUDA when the device is out of memory, and it
+// should come before any stream capture.  From then on the device holds
+// PTEBD_NOALLOC_SCRATCH_BYTES of it until the process exits.
+// Host code cannot use the array's name as a device address, so every call
+// looks the address up with cudaGetSymbolAddress on the current device (cheap
+// once the module is loaded; no cached pointer can outlive a context that the
+// caller tore down and re-created) and checks that the stream belongs to that
+// device.
 // All calls share the array and it keeps the previous call's contents: the
 // counters and error word are cleared on every call, everything else is
 // overwritten before it is read.  Calls whose work overlaps on the GPU (two
 // streams, or two host threads) race on the array and must be serialised by
 // the caller.
-#include <mutex>
-
 #include "ptebd_internal.h"
 
 namespace ptebd {
@@ -34,21 +38,16 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PTEBD_NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_mu;
-constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once).
-int scratch_address(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PTEBD_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PTEBD_ERR_CUDA;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+// Device address of the scratch array on the current device, which must be
+// the device of `stream`.
+int scratch_address(void* stream, void** out) {
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PTEBD_ERR_CUDA;
+    if (cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev) != cudaSuccess) return PTEBD_ERR_CUDA;
+    if (sdev != dev) return PTEBD_ERR_INVALID;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PTEBD_ERR_CUDA;
+    *out = p;
     return PTEBD_OK;
 }
 
@@ -62,7 +61,7 @@ extern "C" int ptebd_svd_batched_noalloc(int32_t precision, int32_t batch, int32
     if (rc) return rc;
     if (need > (size_t)PTEBD_NOALLOC_SCRATCH_BYTES) return PTEBD_ERR_MEMORY;
     void* scratch = nullptr;
-    rc = scratch_address(&scratch);
+    rc = scratch_address(stream, &scratch);
     if (rc) return rc;
     return ptebd::svd_batched_impl(precision, batch, rows, cols, a, lda, sigma, u, ldu, scratch,
                                    (size_t)PTEBD_NOALLOC_SCRATCH_BYTES, stream, check);

@@ -30,6 +30,7 @@ __all__ = [
     "random_one_site_op",
     "gates_to_interleaved",
     "saturated_bond",
+    "trotter_heisenberg_circuit",
 ]
 
 
@@ -108,3 +109,46 @@ def saturated_bond(seed: int, chi: int) -> dict:
 
     return {"lam_l": lam(), "lam_c": lam(), "lam_r": lam(), "gamma_l": gam(), "gamma_r": gam(),
             "gate": haar_u4(rng)}
+
+
+def _haar_u2(rng: np.random.Generator) -> np.ndarray:
+    z = (rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))) / np.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))[None, :]
+
+
+def trotter_heisenberg_circuit(seed: int, n_sites: int, depth: int, dt: float):
+    """Brickwork layers of first-order Trotter steps exp(-i dt h_b) of a Heisenberg
+    chain with random fields, h_b = XX + YY + ZZ + f_b Z(x)1 + f'_b 1(x)Z (f, f'
+    uniform in [-1, 1], fixed per bond), from |0...0> rotated by one Haar-random
+    one-qubit gate per site (folded into the first layer's gates; n_sites even).
+    Near-identity gates on a weakly entangled state: the Schmidt spectra fall
+    off fast, through the range that complex64 arithmetic cannot resolve.
+    Returns the same (parity, bonds, gates) list as brickwork_circuit."""
+    assert n_sites % 2 == 0
+    rng = _rng(seed, 0x7107, n_sites)
+    x = np.array([[0, 1], [1, 0]], complex)
+    y = np.array([[0, -1j], [1j, 0]])
+    z = np.diag([1.0, -1.0]).astype(complex)
+    one = np.eye(2)
+    fields = rng.uniform(-1.0, 1.0, (n_sites - 1, 2))
+    gates_of = []
+    for b in range(n_sites - 1):
+        h = np.kron(x, x) + np.kron(y, y) + np.kron(z, z) + fields[b, 0] * np.kron(z, one) \
+            + fields[b, 1] * np.kron(one, z)
+        w, v = np.linalg.eigh(h)
+        gates_of.append((v * np.exp(-1j * dt * w)[None, :]) @ v.conj().T)
+    rot = [_haar_u2(rng) for _ in range(n_sites)]
+    layers = []
+    for l in range(depth):
+        parity = l % 2
+        bonds = layer_bonds(n_sites, parity)
+        gates = []
+        for b in bonds:
+            u = gates_of[b]
+            if l == 0:
+                u = u @ np.kron(rot[b], rot[b + 1])
+            gates.append(u)
+        layers.append((parity, bonds, np.stack(gates) if gates else np.zeros((0, 4, 4), complex)))
+    return layers

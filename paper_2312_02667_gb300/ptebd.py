@@ -38,16 +38,16 @@ EXPORTS = (
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
-    "ptebd_set_chunk_streams", "ptebd_test_wait_timeout",
+    "ptebd_set_chunk_streams", "ptebd_test_wait_timeout", "ptebd_alu_peak",
 )
-KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor")
+KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor", "resolve")
 
 
 class ptebd_config(ctypes.Structure):
     _fields_ = [
         ("n_sites", ctypes.c_int32), ("d", ctypes.c_int32), ("chi_max", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("g", ctypes.c_int32), ("eps_mode", ctypes.c_int32),
-        ("cutoff", ctypes.c_double), ("floor", ctypes.c_double),
+        ("cutoff", ctypes.c_double), ("resolve", ctypes.c_double),
     ]
 
 
@@ -102,6 +102,7 @@ _SIGS = {
     "ptebd_sample_workspace_bytes": (_P, ctypes.c_int32, _SZ),
     "ptebd_set_chunk_streams": (_P, ctypes.c_int32),
     "ptebd_test_wait_timeout": (_P, ctypes.c_int32),
+    "ptebd_alu_peak": (ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P, _D, _D),
 }
 
 
@@ -139,11 +140,11 @@ def _iptr(a: np.ndarray):
 
 # ---------------------------------------------------------------- C names --
 
-def make_config(n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="schmidt", floor=-1.0):
+def make_config(n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="schmidt", resolve=-1.0):
     prec = {"fp64": PTEBD_FP64, "mixed": PTEBD_MIXED}[precision] if isinstance(precision, str) else int(precision)
     mode = {"schmidt": PTEBD_EPS_SCHMIDT, "relative": PTEBD_EPS_RELATIVE, "absolute": PTEBD_EPS_ABSOLUTE}[eps_mode] \
         if isinstance(eps_mode, str) else int(eps_mode)
-    return ptebd_config(int(n_sites), 2, int(chi_max), prec, int(g), mode, float(cutoff), float(floor))
+    return ptebd_config(int(n_sites), 2, int(chi_max), prec, int(g), mode, float(cutoff), float(resolve))
 
 
 def ptebd_required_bytes(cfg: ptebd_config):
@@ -339,10 +340,11 @@ def ptebd_timing_read(h):
 
 def ptebd_work_counters(h):
     """(Jacobi pair-row visits, theta flops, rotations applied, sweeps summed,
-    SVDs, tSU visits, tSU sweeps, tSU SVDs) since create/reset."""
-    out = np.zeros(8, dtype=np.uint64)
-    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 8), h)
-    return tuple(int(x) for x in out)
+    SVDs, tSU visits, tSU sweeps, tSU SVDs, bonds recomputed in FP64 by the
+    resolution of a mixed state, their Jacobi visits) since create/reset."""
+    out = np.zeros(16, dtype=np.uint64)
+    _check(lib.ptebd_work_counters(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), 16), h)
+    return tuple(int(x) for x in out[:10])
 
 
 def ptebd_svd_workspace_bytes(precision, batch, rows, cols) -> int:
@@ -363,6 +365,32 @@ def ptebd_svd_batched_noalloc(precision, batch, rows, cols, a_ptr, lda, sigma_pt
     _check(lib.ptebd_svd_batched_noalloc(int(precision), int(batch), int(rows), int(cols), _P(a_ptr), int(lda),
                                          _P(sigma_ptr), _P(u_ptr) if u_ptr else None, int(ldu), _P(stream),
                                          int(check)))
+
+
+def ptebd_alu_peak(kind, iters, scratch_ptr, scratch_bytes, stream):
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.ptebd_alu_peak(int(kind), int(iters), _P(scratch_ptr), int(scratch_bytes), _P(stream),
+                              ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
+
+
+ALU_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def alu_peak(kind, target_ms=150.0):
+    """Measured FMA throughput of the current GPU for `kind` in ALU_KINDS:
+    one short launch sizes a second one of about target_ms, whose rate is
+    returned as (TFLOP/s, ms, iterations)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    scratch = torch.empty(8 * sms * 256, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    k = ALU_KINDS[kind]
+    iters = 16
+    _, ms = ptebd_alu_peak(k, iters, scratch.data_ptr(), scratch.numel() * 8, stream)
+    iters = max(16, int(iters * target_ms / max(ms, 1e-3)))
+    tf, ms = ptebd_alu_peak(k, iters, scratch.data_ptr(), scratch.numel() * 8, stream)
+    return tf, ms, iters
 
 
 def svd_batched(a, want_u=False, check=True):
@@ -446,9 +474,9 @@ class State:
     """One MPS on the current CUDA device, its buffers allocated by torch."""
 
     def __init__(self, n_sites, chi_max, precision="mixed", cutoff=1e-12, g=0, eps_mode="schmidt",
-                 floor=-1.0, workspace_bytes=None, stream=None, device=None):
+                 resolve=-1.0, workspace_bytes=None, stream=None, device=None):
         import torch
-        self.cfg = make_config(n_sites, chi_max, precision, cutoff, g, eps_mode, floor)
+        self.cfg = make_config(n_sites, chi_max, precision, cutoff, g, eps_mode, resolve)
         self.n_sites, self.chi_max = int(n_sites), int(chi_max)
         sb, wb, wmin = ptebd_required_bytes(self.cfg)
         if workspace_bytes is not None:

@@ -57,9 +57,14 @@ def test_required_bytes_and_validation(lib_path):
     # whole-layer workspace: 512 slots of two 512x512 complex64 matrices
     assert wb >= 512 * 2 * 512 * 512 * 8
     assert wmin < wb and wmin >= 2 * 512 * 512 * 8
+    # the FP64 resolution adds two 512x512 complex128 matrices per slot
+    assert wb >= 512 * (3 * 512 * 512 * 8 + 2 * 512 * 512 * 16)
+    plain = ptebd.make_config(1024, 256, "mixed", 1e-12, 1, resolve=0.0)
+    sbp, wbp, _ = ptebd.ptebd_required_bytes(plain)
+    assert sbp == sb and wbp <= wb - 512 * 2 * 512 * 512 * 16
     cfg64 = ptebd.make_config(1024, 256, "fp64")
     sb64, wb64, _ = ptebd.ptebd_required_bytes(cfg64)
-    assert sb64 > 1.9 * sb and wb64 > 1.9 * wb
+    assert sb64 > 1.9 * sb and wb64 > 1.9 * wbp
     bad = ptebd.make_config(16, 8)
     bad.d = 3
     with pytest.raises(ptebd.PtebdError) as e:

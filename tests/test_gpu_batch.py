@@ -67,7 +67,7 @@ def test_uneven_circuits_against_oracle(ptebd):
         for i in range(k):
             if layer < ds[i]:
                 parity, bonds, gates = circuits[i][layer]
-                oracle.apply_layer(refs[i], gates, parity, int(chis[i]), 1e-6)
+                oracle.apply_layer(refs[i], gates, parity, int(chis[i]), 1e-12)
                 gl.append(gates)
                 par.append(parity)
             else:
@@ -77,7 +77,7 @@ def test_uneven_circuits_against_oracle(ptebd):
     for i in range(k):
         got = to_oracle(states[i])
         for b in range(int(ns[i]) - 1):
-            compare_spectra(got.lambdas[b], refs[i].lambdas[b], 1e-5, 1e-6, int(chis[i]))
+            compare_spectra(got.lambdas[b], refs[i].lambdas[b], 1e-5, 1e-12, int(chis[i]))
         assert fidelity(got, refs[i]) >= 1 - int(ds[i]) * 1e-6
     batch.close()
 
@@ -125,8 +125,8 @@ def test_batched_serving_64_circuits_sampled_bonds(ptebd):
         eps_g, _, _ = states[i].bond_stats()
         for b, u, ll, gb, lb, gb1, lr in checks[i]:
             mini = mini_vidal(ll, gb, lb, gb1, lr)
-            r = oracle.update_bond(mini, 1, u, chi, 1e-6)
-            compare_spectra(states[i].lam(b), mini.lambdas[1], 1e-5, 1e-6, chi)
+            r = oracle.update_bond(mini, 1, u, chi, 1e-12)
+            compare_spectra(states[i].lam(b), mini.lambdas[1], 1e-5, 1e-12, chi)
             assert abs(eps_g[b] - r.eps) <= 1e-5 * max(r.eps, 1e-3)
     batch.close()
 

@@ -26,7 +26,9 @@ def ptebd():
 
 
 def thr(prec):
-    return 1e-6 if prec == "mixed" else 1e-12
+    """The configured cutoff on both paths (the mixed path resolves undecided
+    bonds in FP64)."""
+    return 1e-12
 
 
 def family_layers(name):

@@ -60,9 +60,11 @@ def test_noalloc_matches_batched(env, prec, shape, tol):
         at = torch.from_numpy(a / np.sqrt(shape[1])).to(dt).cuda()
         s_ref, u_ref, s_na, u_na = run_both(torch, ptebd, fn, at, prec)
         assert np.abs(s_na - s_ref).max() <= tol * s_ref.max()
-        # singular vectors agree up to a phase per column
-        ov = np.abs(np.einsum("bkr,bkr->bk", u_na.conj(), u_ref))
-        assert np.abs(ov - 1).max() <= (2e-5 if prec == 1 else 1e-10)
+        # both entry points run the same kernels on the same data; only the
+        # scratch differs, so leftovers of an earlier call would show up as a
+        # difference in any bit
+        assert np.array_equal(s_na, s_ref)
+        assert np.array_equal(u_na, u_ref)
 
 
 def test_noalloc_rejects_oversize(env):

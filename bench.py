@@ -87,6 +87,15 @@ def parse():
                    help="the batched-serving workload (64 uneven circuits, one graph launch per layer) alone")
     p.add_argument("--routed", action="store_true",
                    help="the 2D routed workload (32x32 lattice, depth 8, chi 128, compiled sparse layers) alone")
+    p.add_argument("--no-tune", action="store_true", help="--serving: skip the autotuned pass")
+    p.add_argument("--serial", action="store_true",
+                   help="--serving: advance the states one by one (no batch graph), for comparison")
+    p.add_argument("--no-tensor-cores", action="store_true",
+                   help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
+    p.add_argument("--resolve", type=float, default=-1.0,
+                   help="mixed: the level below which complex64 singular values are resolved in FP64 (-1: default)")
+    p.add_argument("--qft", action="store_true",
+                   help="the QFT workload (N=96 random MPS, chi 64, the line network of compiled layers) alone")
     p.add_argument("--svd-only", action="store_true",
                    help="micro benchmark instead: the batched Jacobi SVD on 512x512 complex64 matrices")
     return p.parse_args()
@@ -216,7 +225,9 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
     n, chi = args.n_sites, args.chi
-    st = ptebd.State(n, chi, args.precision, cutoff=1e-12, g=args.g)
+    st = ptebd.State(n, chi, args.precision, cutoff=1e-12, g=args.g, resolve=args.resolve)
+    if args.no_tensor_cores:
+        st.set_tensor_cores(False)
     if args.chunk_streams:
         st.set_chunk_streams(args.chunk_streams)
     n_layers = args.prefill + args.warmup + args.steps
@@ -568,10 +579,14 @@ def _timed_run(reset, body):
 def serving_bench(args):
     """Batched serving: 64 independent 1D brickwork circuits of Haar U(4) gates,
     N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256} (the seeded
-    recipe of the batched-serving test), mixed precision, g = 0, advanced together
-    by one CUDA-graph launch per layer (ptebd_batch_apply_layer; gates from host
-    memory).  One untimed pass records the graphs; the timed pass runs the whole
-    set again from reset states."""
+    recipe of the batched-serving test), precision --precision, g = 0, advanced
+    together by one CUDA-graph launch per layer (ptebd_batch_apply_layer; gates
+    from host memory).  Each configuration gets one untimed pass that records
+    the graphs, then a timed pass over the whole set from reset states:
+    first with the library's default launch choices, then after ptebd_autotune
+    has tuned one representative state of every (chi_max, length bucket) at
+    the middle of its circuit and its choice has been given to the other
+    states of that key."""
     import numpy as np
     import torch
 
@@ -581,7 +596,10 @@ def serving_bench(args):
     ns = rng.integers(50, 501, k)
     ds = rng.integers(8, 25, k)
     chis = rng.choice([32, 64, 128, 256], k)
-    states = [ptebd.State(int(ns[i]), int(chis[i]), "mixed") for i in range(k)]
+    states = [ptebd.State(int(ns[i]), int(chis[i]), args.precision, resolve=args.resolve) for i in range(k)]
+    if args.no_tensor_cores:
+        for st in states:
+            st.set_tensor_cores(False)
     circuits_ = [inputs.brickwork_circuit(300 + i, int(ns[i]), int(ds[i]), circuit=i) for i in range(k)]
     layers, gated = [], 0
     for layer in range(int(ds.max())):
@@ -596,26 +614,75 @@ def serving_bench(args):
                 gl.append(None)
                 par.append(-1)
         layers.append((gl, par))
-    batch = ptebd.Batch(states)
 
     def reset():
         for st in states:
             st.reset()
 
-    def body():
-        for gl, par in layers:
-            batch.apply_layer(gl, par)
+    def run_pass():
+        batch = None if args.serial else ptebd.Batch(states)
 
-    first, _ = _timed_run(reset, body)
-    wall, dev = _timed_run(reset, body)
-    batch.close()
+        def body():
+            for gl, par in layers:
+                if batch is not None:
+                    batch.apply_layer(gl, par)
+                else:
+                    for st, g_, p_ in zip(states, gl, par):
+                        if p_ >= 0:
+                            st.apply_layer(g_, p_)
+        first, _ = _timed_run(reset, body)
+        w0 = [st.work_counters()[8] for st in states]
+        wall, dev = _timed_run(reset, body)
+        resolved = sum(st.work_counters()[8] - a for st, a in zip(states, w0))
+        if batch is not None:
+            batch.close()
+        return first, wall, dev, resolved
+
+    first_u, wall_u, dev_u, resolved = run_pass()
+    if args.no_tune:
+        for st in states:
+            st.close()
+        return {"metric": "batched serving: 64 uneven 1D circuits, one graph launch per layer",
+                "unit": "bond-SVDs/s", "value": gated / wall_u, "higher_is_better": True,
+                "untuned": {"value": gated / wall_u, "wall_s": wall_u, "device_s": dev_u, "first_pass_s": first_u},
+                "gated_bond_updates": gated, "fp64_resolved_bonds": resolved, "precision": args.precision,
+                "tensor_cores": not args.no_tensor_cores}
+    # tune one representative per key at the middle of its circuit
+    def key(i):
+        return (int(chis[i]), int(ns[i] - 1).bit_length())
+    reps, choices = {}, {}
+    for i in range(k):
+        reps.setdefault(key(i), i)
+    t0 = time.perf_counter()
+    for kk, i in reps.items():
+        st = states[i]
+        st.reset()
+        half = int(ds[i]) // 2
+        for parity, _, gates in circuits_[i][:half]:
+            st.apply_layer(gates, parity)
+        parity, _, gates = circuits_[i][half]
+        choices[kk] = st.autotune(gates, parity)
+    tune_s = time.perf_counter() - t0
+    for i, st in enumerate(states):
+        nw, chunks, _, _ = choices[key(i)]
+        st.set_jacobi_width(nw)
+        st.set_chunk_streams(chunks)
+    first_t, wall_t, dev_t, _ = run_pass()
+    for st in states:
+        st.close()
     return {"metric": "batched serving: 64 uneven 1D circuits, one graph launch per layer", "unit": "bond-SVDs/s",
-            "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
-            "circuit_layers_per_s": float(ds.sum()) / wall, "batch_layers_per_s": len(layers) / wall,
-            "wall_s": wall, "device_s": dev, "first_pass_s": first, "gated_bond_updates": gated,
+            "value": gated / wall_t, "higher_is_better": True, "n_gpus": 1,
+            "dtype": "c64" if args.precision == "mixed" else "c128", "data": "synthetic",
+            "untuned": {"value": gated / wall_u, "wall_s": wall_u, "device_s": dev_u, "first_pass_s": first_u},
+            "tuned": {"value": gated / wall_t, "wall_s": wall_t, "device_s": dev_t, "first_pass_s": first_t,
+                      "tuning_s": tune_s,
+                      "choices": {f"chi{a}_nbits{b}": {"jacobi_width": c[0], "chunks": c[1]}
+                                  for (a, b), c in choices.items()}},
+            "circuit_layers_per_s": float(ds.sum()) / wall_t, "batch_layers_per_s": len(layers) / wall_t,
+            "gated_bond_updates": gated, "fp64_resolved_bonds": resolved,
             "circuits": k, "circuit_layers": int(ds.sum()), "batch_layers": len(layers),
             "config": {"workload": "64 circuits, N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256}, "
-                                   "Haar U(4) brickwork, cutoff 1e-12, mixed, g = 0, from |0...0>",
+                                   f"Haar U(4) brickwork, cutoff 1e-12, {args.precision}, g = 0, from |0...0>",
                        "seed": 64}}
 
 
@@ -632,7 +699,9 @@ def routed_bench(args):
     lx = ly = 32
     chi = 128
     compiled = circuits2d.compile_layers(lx, ly, circuits2d.physical_layers(4, lx, ly, 8))
-    st = ptebd.State(lx * ly, chi, "mixed")
+    st = ptebd.State(lx * ly, chi, "mixed", resolve=args.resolve)
+    if args.no_tensor_cores:
+        st.set_tensor_cores(False)
     gated = sum(len(b) for b, _ in compiled)
 
     def body():
@@ -641,7 +710,9 @@ def routed_bench(args):
 
     first, _ = _timed_run(st.reset, body)
     wall, dev = _timed_run(st.reset, body)
+    resolved = st.work_counters()[8]
     return {"metric": "2D routed circuit, 32x32 lattice, depth 8, chi 128", "unit": "bond-SVDs/s",
+            "fp64_resolved_bonds": resolved,
             "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
             "ms_per_compiled_layer": 1e3 * wall / len(compiled), "compiled_layers": len(compiled),
             "gated_bond_updates": gated, "wall_s": wall, "device_s": dev, "first_pass_s": first,
@@ -649,6 +720,51 @@ def routed_bench(args):
             "config": {"workload": "32x32 lattice on the snake path, 8 physical layers (ABCD) of Haar U(4) gates, "
                                    "194 compiled layers, chi_max 128, cutoff 1e-12, mixed, g = 0, from |0...0>",
                        "seed": 4}}
+
+
+def qft_bench(args):
+    """The QFT workload of App. B: a random MPS of bond dimension 10 on N = 96
+    qubits (the largest size of the paper's QFT table), brought to canonical
+    form by the library's PtSU steps, then the QFT compiled onto the line
+    (paper_2312_02667_gb300.qft: 2N - 3 = 189 sparse layers of fused
+    SWAP . controlled-phase gates) through ptebd_apply_bonds, chi_max 64,
+    cutoff 1e-12, g = 0 (the paper's setting), mixed precision, gates from host
+    memory.  Timed over the whole network (the paper's time per compiled
+    layer), after one untimed pass; the state is reloaded before each pass."""
+    import torch
+
+    from paper_2312_02667_gb300 import inputs, ptebd, qft
+    n, chi = 96, 64
+    ms = inputs.random_mps_scaled(96, n, 10)
+    lams = [np.ones(m.shape[2]) for m in ms[:-1]]
+    layers = qft.qft_line_layers(n)
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=0, resolve=args.resolve)
+    if args.no_tensor_cores:
+        st.set_tensor_cores(False)
+    gated = sum(len(b) for b, _ in layers)
+
+    def reset():
+        st.reset()
+        st.load(ms, lams)
+        st.canonicalize()
+        st.sync()
+
+    def body():
+        for bonds, us in layers:
+            st.apply_bonds(bonds, us)
+
+    first, _ = _timed_run(reset, body)
+    w0 = st.work_counters()
+    wall, dev = _timed_run(reset, body)
+    w1 = st.work_counters()
+    return {"metric": "QFT on a random MPS, N=96, chi 64 (App. B workload)", "unit": "bond-SVDs/s",
+            "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
+            "ms_per_compiled_layer": 1e3 * wall / len(layers), "compiled_layers": len(layers),
+            "gated_bond_updates": gated, "wall_s": wall, "device_s": dev, "first_pass_s": first,
+            "max_chi": int(max(st.chi())), "fp64_resolved_bonds": w1[8] - w0[8],
+            "config": {"workload": "QFT compiled onto the line by the library's SWAP network (2N-3 layers, "
+                                   "N(N-1)/2 gates) on a canonicalised random MPS of bond dimension 10, N=96, "
+                                   "chi_max 64, cutoff 1e-12, mixed, g = 0", "seed": 96}}
 
 
 def main():
@@ -661,6 +777,9 @@ def main():
         return
     if args.routed:
         print(json.dumps(routed_bench(args)), flush=True)
+        return
+    if args.qft:
+        print(json.dumps(qft_bench(args)), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -99,8 +99,8 @@ typedef struct ptebd_config {
     double cutoff;      /* drop singular values <= cutoff * lambda_1 (>= 0) */
     double resolve;     /* PTEBD_MIXED only (ignored for PTEBD_FP64): complex64
                            singular values <= resolve * lambda_1 are not trusted
-                           (rounding leaves about 1e-7 lambda_1 where the exact
-                           spectrum has zeros); a negative value selects 1e-5.
+                           (rounding leaves up to about 5e-8 lambda_1 where the
+                           exact spectrum has zeros); a negative value selects 1e-6.
                            When resolve > cutoff, a gated or tSU bond whose kept
                            count depends on such values (taken as real or as zero,
                            with the structural bound rank(theta') <=
@@ -166,6 +166,64 @@ int ptebd_regauge(ptebd_state* st, int32_t g);
  * workspace holds fewer slots than the chunks need, while per-kernel timing is
  * on, and for ptebd_apply_bonds lists that are not in ascending order. */
 int ptebd_set_chunk_streams(ptebd_state* st, int32_t n);
+
+/* Precision of the PtSU steps (Sec. III D) of a PTEBD_MIXED state.
+ * PTEBD_MIXED (the default): tSU runs in complex64 like the gate updates, with
+ * the FP64 resolution of undecided bonds; the orthogonality of the regauged
+ * Gamma is then limited by the complex64 Jacobi (about 8 sqrt(rows) 2^-24).
+ * PTEBD_FP64: every tSU bond runs in FP64 (theta formed in FP64 from the
+ * stored complex64 Gamma, FP64 orthogonalisation and Jacobi, Gamma rebuilt in
+ * FP64), so the regauged state is canonical to the rounding of its complex64
+ * storage; it costs the FP64 pipe's time (about 1/64 of the FP32 rate here).
+ * No effect on a PTEBD_FP64 state; PTEBD_ERR_UNSUPPORTED when the state has
+ * no FP64 workspace (config resolve <= cutoff). */
+int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision);
+
+/* Polish sweep of the complex64 Jacobi SVDs (the SVD of the TEBD procedure,
+ * Sec. II C; no effect on complex128 SVDs).  The sweeps stop when no pair has
+ * |a^H b| > 8 sqrt(rows) 2^-24 |a| |b| (or every rotation of a sweep was
+ * small), which leaves the kept singular vectors orthogonal to about that
+ * level; the truncated two-site state then carries a relative error of a few
+ * 1e-5.  mode 1: the gated SVDs end with one more sweep at 2 sqrt(rows)
+ * 2^-24, mode 2 (the default): the tSU SVDs as well, mode 0: none.  Measured
+ * on one saturated layer with PtSU (N = 256, chi = 256) against the FP64 path:
+ * 1 - F = 5.6e-7 (mode 0), 4.5e-7 (mode 1), 4.7e-8 (mode 2) for 9% more time. */
+int ptebd_set_svd_polish(ptebd_state* st, int32_t mode);
+
+/* Tensor cores for the two-site tensor of a PTEBD_MIXED state (no counterpart
+ * in the paper: a choice of arithmetic unit).  enable != 0 (the default): when
+ * chi_max rounded up (16 * 2^k) is at least 64, theta' = U theta is formed by
+ * tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory, operands
+ * split as hi + lo TF32 pairs and multiplied hi*hi + hi*lo + lo*hi (FP32
+ * accuracy); enable = 0: FP32 FMAs on the CUDA cores.  The two round
+ * differently (both to FP32 accuracy).  No effect on PTEBD_FP64 states. */
+int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable);
+
+/* Jacobi block width of the handle's SVDs (no counterpart in the paper: a
+ * launch choice): the columns held in registers by one CTA, one per warp.
+ * complex64: 16 (default) or 8; complex128: always 8.  0 selects the default.
+ * Results are bit-identical run to run for a given width; two widths visit
+ * the column pairs in different orders and so differ by rounding (both within
+ * the SVD's accuracy). */
+int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw);
+
+/* Autotuner (no counterpart in the paper: a scheduling choice of the library).
+ * Times every candidate launch configuration on the state's own next layer
+ * (the gates and parity a ptebd_apply_layer call would get, with the config's
+ * PtSU steps): Jacobi block width (complex64: 16 and 8) x bond chunks (1, 2,
+ * 4, 8, 12, 16, those the workspace can run concurrently); each candidate runs
+ * twice from the saved state and the second run is timed with CUDA events on
+ * the handle's stream.  The state is copied into `scratch` (device memory,
+ * 256-byte aligned, at least state_bytes of ptebd_required_bytes, owned by
+ * the caller) first and restored before every run and at the end, so the call
+ * leaves the state, its counters and its layer count as it found them.  The
+ * fastest configuration is set on the handle and remembered for the process
+ * under (chi_max padded, precision, bit length of N - 1, g): later
+ * ptebd_create calls with the same key start with it.  best (may be NULL):
+ * [block width, chunks, ms of the best, ms of the configuration the handle
+ * had (-1 if it was not among the candidates)].  Synchronous. */
+int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t gates_on_device,
+                   void* scratch, size_t scratch_bytes, double* best);
 
 /* Test of the failure detection (no counterpart in the paper).  With enable
  * != 0, in every later SVD launch one warp of each CTA waits, in its first
@@ -246,8 +304,9 @@ int ptebd_timing_read(ptebd_state* st, double* ms, int32_t* launches, int32_t n_
  * out[3] = Jacobi sweeps summed over every SVD; out[4] = number of SVDs;
  * out[5..7] = the same three counts (visits, sweeps, SVDs) for the Jacobi runs
  * of the tSU steps alone (out[0..7] count the state's own precision only);
- * out[8] = bonds recomputed in FP64 by the resolution of a PTEBD_MIXED state
- * (gated and tSU), out[9] = the Jacobi visits of those FP64 runs.
+ * out[8] = bonds of a PTEBD_MIXED state computed in FP64 (by the resolution,
+ * gated and tSU, and by an FP64 regauge), out[9] = the Jacobi visits of
+ * those FP64 runs.
  * n entries are written (<= 16; out[10..15] are reserved and read 0). */
 int ptebd_work_counters(ptebd_state* st, uint64_t* out, int32_t n);
 

@@ -3,6 +3,9 @@
 // host side of the contractions.  All device work is issued on the handle's
 // stream; the library never allocates device memory.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,6 +45,11 @@ struct ptebd_state {
     cudaEvent_t fork_ev = nullptr;
     int chunk_streams = 0;  // requested number of chunks (0: chosen from N)
     int wait_test = 0;      // see ptebd_test_wait_timeout
+    bool regauge64 = false; // PTEBD_MIXED: tSU stages run in FP64 (ptebd_set_regauge_precision)
+    int jacobi_nw = 0;      // Jacobi block width (0: default; see ptebd_set_jacobi_width)
+    int tensor_cores = 1;   // complex64 theta' on the tensor cores (ptebd_set_tensor_cores)
+    int polish = 2;         // complex64 Jacobi polish sweep: 0 none, 1 gated SVDs, 2 gated and tSU
+    cudaStream_t body_stream = nullptr;  // captures the bodies of the FP64 pass's IF nodes (owned)
     // set once a device error says that a CTA returned with its own bulk copies still in
     // flight (DERR_DRAIN): the state and its workspace can no longer be trusted, and
     // every later call that launches work on it fails until it is destroyed
@@ -51,6 +59,7 @@ struct ptebd_state {
         for (cudaEvent_t e : chunk_ev) cudaEventDestroy(e);
         if (fork_ev) cudaEventDestroy(fork_ev);
         for (cudaStream_t x : aux) cudaStreamDestroy(x);
+        if (body_stream) cudaStreamDestroy(body_stream);
     }
 };
 
@@ -58,10 +67,12 @@ namespace ptebd {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Complex64 singular values below 1e-5 sigma_1 are not trusted by default: the
-// rounding of theta' and of the rotations leaves values of about 1e-7 sigma_1
-// where the exact spectrum has zeros.
-constexpr double kResolveDefault = 1e-5;
+// Complex64 singular values at or below 1e-6 sigma_1 are not trusted by default:
+// where the exact spectrum has zeros, the rounding of theta' and of the
+// rotations leaves values of up to about 5e-8 sigma_1 (measured on Trotter,
+// CZ and SWAP-routed circuits), while real values above 1e-6 sigma_1 come out
+// with relative errors below 1e-2 (graded spectra keep their relative accuracy).
+constexpr double kResolveDefault = 1e-6;
 
 static int chip_for(int chi_max) {
     int c = 16;
@@ -308,6 +319,9 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     a.eps_mode = st->cfg.eps_mode;
     a.stabilise = gated ? 1 : 0;
     a.max_sweeps = 40;
+    a.nw = st->jacobi_nw;
+    a.tensor_cores = st->tensor_cores;
+    a.polish = (gated && st->polish >= 1) || (!gated && st->polish >= 2) ? 1 : 0;
     a.wait_test = st->wait_test;
     a.bond_eps = at<double>(m, L.off_bond_eps);
     a.bond_nu = at<double>(m, L.off_bond_nu);
@@ -351,7 +365,7 @@ LayerArgs<double> refine_args(ptebd_state* st, const LayerArgs<float>& c, int ba
     a.thr_rel = st->cfg.cutoff;
     a.resolve = 0.0;
     a.refine = 1;
-    a.eps_mode = c.eps_mode; a.stabilise = c.stabilise; a.max_sweeps = c.max_sweeps; a.wait_test = 0;
+    a.eps_mode = c.eps_mode; a.stabilise = c.stabilise; a.max_sweeps = c.max_sweeps; a.wait_test = 0; a.nw = 0;
     a.mode = c.mode; a.pass = 0;
     a.bond_eps = c.bond_eps; a.bond_nu = c.bond_nu; a.bond_rank = c.bond_rank; a.bond_sweeps = c.bond_sweeps;
     a.totals = c.totals; a.err = c.err; a.work = c.work;
@@ -393,12 +407,72 @@ int launch_pass(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&&
 // resolution the FP64 pass over the undecided bonds follows, then the sums.
 template <typename R, typename W>
 int launch_chain(ptebd_state* st, LayerArgs<R> a, int base, bool gated, cudaStream_t s, W&& wrap) {
-    int rc = launch_pass<R, cx_t<R>>(st, a, gated, s, wrap);
-    if (rc) return rc;
+    int rc = PTEBD_OK;
+    bool done = false;
     if constexpr (std::is_same<R, float>::value) {
-        if (st->L.resolve64) {
-            rc = launch_pass<double, float2>(st, refine_args(st, a, base), gated, s, wrap);
+        if (!gated && st->regauge64) {  // the whole tSU stage in FP64
+            LayerArgs<double> f = refine_args(st, a, base);
+            f.refine = 2;
+            rc = launch_pass<double, float2>(st, f, gated, s, wrap);
             if (rc) return rc;
+            done = true;
+        }
+    }
+    if (!done) {
+        // The FP64 resolution pass runs only for bonds the complex64 truncation
+        // leaves undecided, which it usually leaves none.  Launched directly, its
+        // CTAs return at once; inside a stream capture (the batch graphs) it
+        // becomes an IF node that the truncation switches on, so that a graph of
+        // many small states launches no idle kernels (they would wait for whole
+        // SMs behind the other states' Jacobi CTAs).
+        bool as_if = false;
+        if constexpr (std::is_same<R, float>::value) {
+            if (st->L.resolve64) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                CUDA_TRY(st, cudaStreamIsCapturing(s, &cs));
+                if (cs == cudaStreamCaptureStatusActive) {
+                    cudaGraph_t g = nullptr;
+                    CUDA_TRY(st, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+                    cudaGraphConditionalHandle h = 0;
+                    CUDA_TRY(st, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+                    a.cond = h;
+                    as_if = true;
+                }
+            }
+        }
+        rc = launch_pass<R, cx_t<R>>(st, a, gated, s, wrap);
+        if (rc) return rc;
+        if constexpr (std::is_same<R, float>::value) {
+            if (st->L.resolve64 && !as_if) {
+                rc = launch_pass<double, float2>(st, refine_args(st, a, base), gated, s, wrap);
+                if (rc) return rc;
+            } else if (as_if) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                cudaGraph_t g = nullptr;
+                const cudaGraphNode_t* deps = nullptr;
+                const cudaGraphEdgeData* edges = nullptr;
+                size_t nd = 0;
+                CUDA_TRY(st, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd));
+                cudaGraphNodeParams p{};
+                p.type = cudaGraphNodeTypeConditional;
+                p.conditional.handle = a.cond;
+                p.conditional.type = cudaGraphCondTypeIf;
+                p.conditional.size = 1;
+                cudaGraphNode_t node = nullptr;
+                CUDA_TRY(st, cudaGraphAddNode(&node, g, deps, edges, nd, &p));
+                cudaGraph_t body = p.conditional.phGraph_out[0];
+                CUDA_TRY(st, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+                CUDA_TRY(st, cudaStreamBeginCaptureToGraph(st->body_stream, body, nullptr, nullptr, 0,
+                                                           cudaStreamCaptureModeRelaxed));
+                LayerArgs<double> f = refine_args(st, a, base);
+                f.cond = 0;
+                rc = launch_pass<double, float2>(st, f, gated, st->body_stream, wrap);
+                cudaGraph_t out = nullptr;
+                const cudaError_t e = cudaStreamEndCapture(st->body_stream, &out);
+                if (rc) return rc;
+                if (e != cudaSuccess)
+                    return set_err(st, PTEBD_ERR_CUDA, "capturing the FP64 pass failed: %s", cudaGetErrorString(e));
+            }
         }
     }
     CUDA_TRY(st, wrap(PTEBD_K_REDUCE, [&] {
@@ -782,6 +856,26 @@ struct ptebd_batch {
     }
 };
 
+// Launch configurations chosen by ptebd_autotune, remembered for the process
+// and applied by ptebd_create to states of the same shape.
+struct TuneKey {
+    int chip, precision, n_sites, g;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(chip, precision, n_sites, g) < std::tie(o.chip, o.precision, o.n_sites, o.g);
+    }
+};
+struct TuneChoice { int nw, chunks; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tuned;
+
+// N enters by its bucket (the bit length of N - 1): states of similar length
+// split into the same chunks and share a choice.
+TuneKey tune_key(const ptebd_state* st) {
+    int bucket = 0;
+    for (int v = st->cfg.n_sites - 1; v > 0; v >>= 1) ++bucket;
+    return TuneKey{st->L.chip, st->cfg.precision, bucket, st->cfg.g};
+}
+
 // =================================================================== ABI ==
 extern "C" {
 
@@ -824,14 +918,28 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
     cudaGetDevice(&st->device);
     cudaError_t e = cfg->precision == PTEBD_FP64 ? jacobi_prepare<double>() : jacobi_prepare<float>();
     if (e == cudaSuccess) e = cfg->precision == PTEBD_FP64 ? orth_prepare<double>() : orth_prepare<float>();
+    if (e == cudaSuccess && cfg->precision == PTEBD_MIXED) e = theta_tc_prepare();
     if (e == cudaSuccess && L.resolve64) e = jacobi_prepare<double>();
     if (e == cudaSuccess && L.resolve64) e = orth_prepare<double>();
     if (e != cudaSuccess) {
         delete st;
         return PTEBD_ERR_CUDA;
     }
+    if (L.resolve64 && cudaStreamCreateWithFlags(&st->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete st;
+        return PTEBD_ERR_CUDA;
+    }
     rc = ptebd_reset(st);
     if (!rc) rc = ensure_chunk_streams(st, chunk_plan(L, 0).k);  // created here, never during a capture
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned.find(tune_key(st));
+        if (it != g_tuned.end()) {
+            st->jacobi_nw = it->second.nw;
+            st->chunk_streams = it->second.chunks;
+        }
+    }
+    if (!rc) rc = ensure_chunk_streams(st, chunk_plan(L, st->chunk_streams).k);
     if (rc) {
         delete st;
         return rc;
@@ -840,9 +948,131 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
     return PTEBD_OK;
 }
 
+int ptebd_set_svd_polish(ptebd_state* st, int32_t mode) {
+    if (!st || mode < 0 || mode > 2) return set_err(st, PTEBD_ERR_INVALID, "polish mode must be 0, 1 or 2");
+    st->polish = mode;
+    return PTEBD_OK;
+}
+
+int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable) {
+    if (!st) return PTEBD_ERR_INVALID;
+    st->tensor_cores = enable ? 1 : 0;
+    return PTEBD_OK;
+}
+
+int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (nw != 0 && nw != 8 && nw != 16) return set_err(st, PTEBD_ERR_INVALID, "Jacobi block width must be 0, 8 or 16");
+    st->jacobi_nw = nw;
+    return PTEBD_OK;
+}
+
+int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t gates_on_device, void* scratch,
+                   size_t scratch_bytes, double* best) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (parity != 0 && parity != 1) return set_err(st, PTEBD_ERR_INVALID, "parity must be 0 or 1");
+    if (!scratch || scratch_bytes < st->L.state_bytes || ((uintptr_t)scratch & 255))
+        return set_err(st, PTEBD_ERR_MEMORY, "autotune needs a 256-byte aligned scratch of state_bytes (%zu)",
+                       st->L.state_bytes);
+    if (st->poisoned) return refuse_poisoned(st);
+    const int nb = n_parity_bonds(st->L.n_sites, parity);
+    if (nb > 0 && !gates) return set_err(st, PTEBD_ERR_INVALID, "null gates");
+    int rc = sync_and_check(st);
+    if (rc) return rc;
+    // candidates: block widths x chunk counts the workspace can run concurrently
+    std::vector<int> widths = {0};
+    if (st->cfg.precision == PTEBD_MIXED) widths = {16, 8};
+    std::vector<int> chunks;
+    for (int k : {1, 2, 4, 8, 12, 16}) {
+        const ChunkPlan p = chunk_plan(st->L, k);
+        if (p.k == k && (k == 1 || st->slots >= p.k * p.cap)) chunks.push_back(k);
+    }
+    const int saved_nw = st->jacobi_nw, saved_chunks = st->chunk_streams;
+    const bool saved_timing = st->timing;
+    st->timing = false;
+    CUDA_TRY(st, cudaMemcpyAsync(scratch, st->mem, st->L.state_bytes, cudaMemcpyDeviceToDevice, st->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(st, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return set_err(st, PTEBD_ERR_CUDA, "event creation failed");
+    }
+    double best_ms = 1e300, default_ms = -1.0;
+    int best_nw = saved_nw, best_chunks = saved_chunks;
+    const int def_nw = jacobi_block_width(st->cfg.precision, saved_nw);
+    const int def_k = chunk_plan(st->L, saved_chunks).k;
+    for (int nw : widths) {
+        for (int k : chunks) {
+            st->jacobi_nw = nw;
+            st->chunk_streams = k;
+            if ((rc = ensure_chunk_streams(st, chunk_plan(st->L, k).k))) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !rc; ++rep) {  // the second run is timed
+                if (cudaMemcpyAsync(st->mem, scratch, st->L.state_bytes, cudaMemcpyDeviceToDevice, st->stream) !=
+                    cudaSuccess) {
+                    rc = set_err(st, PTEBD_ERR_CUDA, "state restore failed");
+                    break;
+                }
+                const double* dg = stage_gates(st, gates, nb, gates_on_device, &rc);
+                if (rc) break;
+                const int32_t* lists = at<int32_t>(st->mem, st->L.off_bonds);
+                const Stage gs{lists + (parity ? st->L.max_bonds : 0), nullptr, parity, nb, dg, true};
+                if (cudaEventRecord(e0, st->stream) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+                if (!rc) rc = run_layer(st, &gs, st->cfg.g);
+                if (!rc && cudaEventRecord(e1, st->stream) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PTEBD_ERR_CUDA;
+                if (!rc) rc = check_device_errors(st);
+            }
+            if (rc) break;
+            if (jacobi_block_width(st->cfg.precision, nw) == def_nw && k == def_k) default_ms = ms;
+            if (ms < best_ms) { best_ms = ms; best_nw = nw; best_chunks = k; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the state as it was, whatever happened above
+    const cudaError_t er = cudaMemcpyAsync(st->mem, scratch, st->L.state_bytes, cudaMemcpyDeviceToDevice, st->stream);
+    const cudaError_t es = cudaStreamSynchronize(st->stream);
+    st->timing = saved_timing;
+    if (rc) {
+        st->jacobi_nw = saved_nw;
+        st->chunk_streams = saved_chunks;
+        ensure_chunk_streams(st, chunk_plan(st->L, saved_chunks).k);
+        return rc;
+    }
+    if (er != cudaSuccess || es != cudaSuccess) return set_err(st, PTEBD_ERR_CUDA, "state restore failed");
+    st->jacobi_nw = best_nw;
+    st->chunk_streams = best_chunks;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tuned[tune_key(st)] = TuneChoice{best_nw, best_chunks};
+    }
+    if (best) {
+        best[0] = jacobi_block_width(st->cfg.precision, best_nw);
+        best[1] = best_chunks ? best_chunks : chunk_plan(st->L, 0).k;
+        best[2] = best_ms;
+        best[3] = default_ms;
+    }
+    return ensure_chunk_streams(st, chunk_plan(st->L, best_chunks).k);
+}
+
 int ptebd_test_wait_timeout(ptebd_state* st, int32_t enable) {
     if (!st) return PTEBD_ERR_INVALID;
     st->wait_test = enable ? 1 : 0;
+    return PTEBD_OK;
+}
+
+int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (precision != PTEBD_FP64 && precision != PTEBD_MIXED)
+        return set_err(st, PTEBD_ERR_INVALID, "precision must be PTEBD_FP64 or PTEBD_MIXED");
+    if (st->cfg.precision == PTEBD_FP64) return PTEBD_OK;  // already FP64 throughout
+    if (precision == PTEBD_FP64 && !st->L.resolve64)
+        return set_err(st, PTEBD_ERR_UNSUPPORTED,
+                       "an FP64 regauge needs the FP64 workspace of the resolution (config resolve > cutoff)");
+    st->regauge64 = precision == PTEBD_FP64;
     return PTEBD_OK;
 }
 

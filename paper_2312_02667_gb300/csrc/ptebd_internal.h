@@ -94,10 +94,16 @@ struct LayerArgs {
                       // complex64 spectrum decides a bond without the FP64 resolution
     double resolve;   // > thr_rel: bonds whose kept count depends on singular values <= resolve * sigma_1
                       // are left undecided (dims D_REFINE = 1) for the FP64 resolution; 0: off
-    int refine;       // 1: this launch is the FP64 resolution pass (only bonds with D_REFINE = 1 run)
+    unsigned long long cond;  // in a stream capture: the conditional handle of the IF node that holds the FP64
+                              // resolution pass; the complex64 truncation sets it when it leaves a bond undecided
+    int refine;       // 1: this launch is the FP64 resolution pass (only bonds with D_REFINE = 1 run);
+                      // 2: an FP64 pass over every bond of a complex64 state (FP64 regauge)
     int eps_mode, stabilise, max_sweeps;
     int wait_test;    // test of the bounded waits: one hand-off wait per CTA targets a count nothing
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
+    int nw;           // Jacobi block width requested (0: the default; 8 or 16 for complex64)
+    int tensor_cores; // complex64 theta' on the tensor cores (tcgen05, 3xTF32) when chip >= 64
+    int polish;       // complex64 Jacobi: one last sweep at the tighter threshold (see Eps::polish)
     int mode;         // 0: gated bond; 1: tSU through the rank-chi_b factorisation
     int pass;         // Jacobi: 0 = rows/cols from dims, 1 = the X factor (2 chi_{b-1} x chi_b)
     double* bond_eps; double* bond_nu; int32_t* bond_rank; int32_t* bond_sweeps;
@@ -108,8 +114,9 @@ struct LayerArgs {
 };
 
 // dims[] entries of a slot (kDims int32 per slot)
+// D_COND (first slot of a launch only): set once the launch has asked for its FP64 pass
 enum { D_CL = 0, D_CM = 1, D_CR = 2, D_TALL = 3, D_BOND = 4, D_K = 5, D_ROWS = 6, D_COLS = 7,
-       D_REFINE = 8 };
+       D_REFINE = 8, D_COND = 9 };
 constexpr int kDims = 16;
 constexpr int kWork = 16;  // work counters
 
@@ -117,6 +124,11 @@ constexpr int kWork = 16;  // work counters
 // G: the complex type of the Gamma store (cx_t<R> except in the FP64 resolution)
 template <typename R, typename G = cx_t<R>> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s);
+// theta' of a complex64 state on the tensor cores (ptebd_theta_tc.cu)
+cudaError_t launch_theta_tc(const LayerArgs<float>& a, cudaStream_t s);
+cudaError_t launch_gamma_gemm_tc(const LayerArgs<float>& a, cudaStream_t s);  // the GEMM factor of the Gamma rebuild
+cudaError_t launch_proj_tc(const LayerArgs<float>& a, cudaStream_t s);        // M^dag of the tSU factorisation
+cudaError_t theta_tc_prepare();  // raises the smem limits of both tensor-core kernels
 template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R, typename G = cx_t<R>> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R, typename G = cx_t<R>> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
@@ -132,7 +144,8 @@ cudaError_t launch_add_partials(const double* partials, int k, double* totals, c
 // A layer may run as up to kMaxChunks bond chunks on concurrent streams.
 constexpr int kMaxChunks = 16;
 template <typename R> cudaError_t jacobi_prepare();   // raises the dynamic smem limit
-size_t jacobi_smem_bytes(int precision, int ldw);
+int jacobi_block_width(int precision, int requested);  // the NW a launch with a.nw = requested uses
+size_t jacobi_smem_bytes(int precision, int ldw, int nw);
 
 // Transfer-matrix contraction.  C = rowscale o (op(A) B) o colscale * alpha + beta C,
 // all column-major; A and B are complex of type TA/TB, C is complex128.

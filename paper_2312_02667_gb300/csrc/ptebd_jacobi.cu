@@ -127,17 +127,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 template <typename R> struct Eps;
 // range_e: matrices whose largest entry is not in [2^-range_e, 2^range_e) are
 // rescaled before the sweeps (see the range guard in jacobi_body).
+// polish: the factor of a last sweep's tighter threshold (A.polish), run once
+// after the stopping rule has fired: it rotates every pair with
+// |a^H b| > polish sqrt(rows) u |a| |b|, which leaves the columns orthogonal to
+// near the rounding of their storage (the truncated state depends on it).
 template <> struct Eps<float> {
     static constexpr double u = 5.9604644775390625e-08;  // 2^-24
     static constexpr double k = 8.0;
     static constexpr int range_e = 24;
     static constexpr double early = 256.0;
+    static constexpr double polish = 2.0;
 };
 template <> struct Eps<double> {
     static constexpr double u = 1.1102230246251565e-16;  // 2^-53
     static constexpr double k = 4.0;
     static constexpr int range_e = 240;
     static constexpr double early = 0.0;
+    static constexpr double polish = 0.0;
 };
 
 template <typename R>
@@ -477,8 +483,10 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     double* nrm2 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(skey + kSortN) + 7) & ~uintptr_t(7));
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
-    const R tol2 = tol * tol;
+    R tol2 = tol * tol;
     const R big2 = (R)Eps<R>::early * tol2;
+    const bool polish = A.polish && Eps<R>::polish > 0.0;
+    bool polishing = false;  // the last sweep, with the tighter threshold
     bool big_w = false;  // this warp rotated a pair with cos^2 >= big2 in the sweep
     const int nb = (cols + NW - 1) / NW;
     const uint32_t col_bytes = (uint32_t)(rows * sizeof(C));
@@ -607,6 +615,10 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             }
         }
         for (int I = 0; I < nb; ++I) {
+            // the polish sweep leaves pairs of two columns beyond chi_max (in the sweep
+            // order, by decreasing norm) alone: they are dropped together, a rotation
+            // between them changes no kept column and keeps their summed weight
+            if (polishing && A.chi_max > 0 && I * NW >= A.chi_max) break;
             // all earlier bulk stores must have landed before plain loads of block I
             if (tid == 0) { bulk_wait_all(); fence_async_global(); }
             __syncthreads();
@@ -729,7 +741,18 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
         const bool small = Eps<R>::early > 0.0 && sh[7] == 0;
         rot_total += rot;
         __syncthreads();
-        if (rot == 0 || small) { converged = true; ++sweep; break; }
+        if (polishing) { converged = true; ++sweep; break; }
+        if (rot == 0 || small) {
+            if (polish) {
+                polishing = true;
+                const R pt = (R)(Eps<R>::polish * sqrt((double)rows) * Eps<R>::u);
+                tol2 = pt * pt;
+                continue;
+            }
+            converged = true;
+            ++sweep;
+            break;
+        }
     }
     if (tid == 0) { bulk_wait_all(); fence_async_global(); }
     __syncthreads();
@@ -796,7 +819,7 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int j = blockIdx.x;
     const int32_t* d = A.dims + j * kDims;
-    if (A.refine && d[D_REFINE] != 1) return;  // the FP64 resolution runs only undecided bonds
+    if (A.refine == 1 && d[D_REFINE] != 1) return;  // the FP64 resolution runs only undecided bonds
     const int rows = A.pass == 1 ? 2 * d[D_CL] : d[D_ROWS];
     const int cols = A.pass == 1 ? d[D_CM] : d[D_COLS];
     C* W = A.w + (size_t)j * A.ldw * A.ldw;
@@ -822,14 +845,21 @@ __global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
     else jacobi_body<R, NW, 16>(A, W, rows, cols, j, smem);
 }
 
+// Block width (columns of the register block = warps of the CTA).  complex64:
+// 16 by default, 8 selectable (a.nw); complex128: 8 (16 columns of complex128
+// stages would not fit in shared memory).
 template <typename R> struct JacobiNW;
 template <> struct JacobiNW<float> { static constexpr int v = 16; };
 template <> struct JacobiNW<double> { static constexpr int v = 8; };
 
 }  // namespace
 
-size_t jacobi_smem_bytes(int precision, int ldw) {
-    const int nw = precision == PTEBD_FP64 ? JacobiNW<double>::v : JacobiNW<float>::v;
+int jacobi_block_width(int precision, int requested) {
+    if (precision == PTEBD_FP64) return JacobiNW<double>::v;
+    return requested == 8 ? 8 : JacobiNW<float>::v;
+}
+
+size_t jacobi_smem_bytes(int precision, int ldw, int nw) {
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
     return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (kShInts + 2 * nw) * sizeof(int) +
@@ -837,16 +867,24 @@ size_t jacobi_smem_bytes(int precision, int ldw) {
 }
 
 template <typename R> cudaError_t jacobi_prepare() {
+    const int prec = std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED;
     constexpr int NW = JacobiNW<R>::v;
-    const size_t need = jacobi_smem_bytes(std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED,
-                                          2 * PTEBD_CHI_LIMIT);
-    return cudaFuncSetAttribute(k_jacobi<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, NW));
+    if (e == cudaSuccess && std::is_same<R, float>::value)
+        e = cudaFuncSetAttribute(k_jacobi<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, 8));
+    return e;
 }
 
 template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStream_t s) {
-    constexpr int NW = JacobiNW<R>::v;
-    const size_t smem = jacobi_smem_bytes(std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED, a.ldw);
-    k_jacobi<R, NW><<<a.count, NW * 32, smem, s>>>(a);
+    const int prec = std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED;
+    const int nw = jacobi_block_width(prec, a.nw);
+    const size_t smem = jacobi_smem_bytes(prec, a.ldw, nw);
+    if (nw == 8)
+        k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);
+    else
+        k_jacobi<R, 16><<<a.count, 16 * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 //                through one complex GEMM with the kept theta';
 //   k_reduce   : deterministic per-layer sums of eps_b and ln nu_b.
 #include <cmath>
+#include <type_traits>
 
 #include "ptebd_internal.h"
 
@@ -45,13 +46,15 @@ template <typename C> __device__ __forceinline__ void cfma_cj(C& acc, C x, C y) 
 // or its adjoint (wide) into w and w0.
 // G: the complex type of the Gamma store, read as is and widened to C (the FP64
 // resolution of a complex64 state forms theta' in FP64 from complex64 Gamma).
-// In the resolution pass (a.refine) only bonds marked undecided run, and their
-// dims (written by the first pass, unchanged since) are left alone.
+// In the resolution pass (a.refine == 1) only bonds marked undecided run, and
+// their dims (written by the first pass, unchanged since) are left alone; with
+// a.refine == 2 (an FP64 pass over every bond: the FP64 regauge of a complex64
+// state) every bond runs and is marked.
 template <typename R, typename G>
 __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z;
-    if (a.refine && a.dims[j * kDims + D_REFINE] != 1) return;
+    if (a.refine == 1 && a.dims[j * kDims + D_REFINE] != 1) return;
     const int b = a.bonds[j];
     const int chip = a.chip;
     // device-side argument check: a bond or dimension out of range (a corrupted
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     // rows and columns make the SVD, truncation and Gamma kernels do nothing
     if (b < 0 || b > a.n_sites - 2 || a.chi[b] < 1 || a.chi[b] > chip || a.chi[b + 1] < 1 ||
         a.chi[b + 1] > chip || a.chi[b + 2] < 1 || a.chi[b + 2] > chip) {
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !a.refine) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.refine != 1) {
             int32_t* d = a.dims + j * kDims;
             for (int q = 0; q < kDims; ++q) d[q] = 0;
             d[D_TALL] = 1;
@@ -70,11 +73,12 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
     // tSU (mode 1) always stores theta^dag: its SVD goes through the factors
     const bool tall = a.mode == 0 && cl >= cr;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && !a.refine) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.refine != 1) {
         int32_t* d = a.dims + j * kDims;
         d[D_CL] = cl; d[D_CM] = cm; d[D_CR] = cr; d[D_TALL] = tall ? 1 : 0; d[D_BOND] = b;
         d[D_K] = 0;
-        d[D_REFINE] = 0;
+        d[D_REFINE] = a.refine == 2 ? 1 : 0;
+        d[D_COND] = 0;
         if (a.mode == 0) { d[D_ROWS] = tall ? 2 * cl : 2 * cr; d[D_COLS] = tall ? 2 * cr : 2 * cl; }
         else { d[D_ROWS] = 2 * cr; d[D_COLS] = cm; }
         atomicAdd(&a.work[1], 32ull * (unsigned long long)cl * (unsigned long long)cm * (unsigned long long)cr);
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
     __shared__ int kept_sh, kept_hi_sh, rmax_sh;
     const int j = blockIdx.x, t = threadIdx.x;
     int32_t* d = a.dims + j * kDims;
-    if (a.refine && d[D_REFINE] != 1) return;
+    if (a.refine == 1 && d[D_REFINE] != 1) return;
     const int ncols = d[D_COLS];
     const int b = d[D_BOND];
     const double* nrm = a.norms + (size_t)j * a.ldw;
@@ -336,6 +340,8 @@ __global__ void __launch_bounds__(512) k_truncate(LayerArgs<R> a) {
                 d[D_K] = 0;  // the Gamma kernels of this pass skip the bond
                 a.slot_eps[j] = 0.0;
                 a.slot_lognu[j] = 0.0;
+                // in a CUDA graph the FP64 pass is an IF node: switch it on, once per launch
+                if (a.cond && atomicExch(&a.dims[D_COND], 1) == 0) cudaGraphSetConditional(a.cond, 1);
             }
             return;
         }
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(256) k_gamma_direct(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z, sg = blockIdx.y;
     const int32_t* d = a.dims + j * kDims;
-    if (a.refine && d[D_REFINE] != 1) return;
+    if (a.refine == 1 && d[D_REFINE] != 1) return;
     const int k = d[D_K];
     if (k == 0) return;  // error latched by k_truncate
     const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND];
@@ -445,7 +451,7 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z >> 1, sg = blockIdx.z & 1;
     const int32_t* d = a.dims + j * kDims;
-    if (a.refine && d[D_REFINE] != 1) return;
+    if (a.refine == 1 && d[D_REFINE] != 1) return;
     const int k = d[D_K];
     if (k == 0) return;
     const int cl = d[D_CL], cr = d[D_CR], b = d[D_BOND], rows = d[D_ROWS];
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(256) k_xform(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.y;
     const int32_t* d = a.dims + j * kDims;
-    if (a.refine && d[D_REFINE] != 1) return;
+    if (a.refine == 1 && d[D_REFINE] != 1) return;
     const int cl = d[D_CL], cm = d[D_CM], b = d[D_BOND];
     const int chip = a.chip;
     const size_t e = (size_t)blockIdx.x * 256 + threadIdx.x;
@@ -574,7 +580,7 @@ __global__ void __launch_bounds__(256) k_proj(LayerArgs<R> a) {
     using C = cx_t<R>;
     const int j = blockIdx.z;
     const int32_t* d = a.dims + j * kDims;
-    if (a.refine && d[D_REFINE] != 1) return;
+    if (a.refine == 1 && d[D_REFINE] != 1) return;
     const int cl = d[D_CL], cm = d[D_CM], cr = d[D_CR];
     const int rows = 2 * cr, kdim = 2 * cl;
     const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
@@ -658,6 +664,8 @@ __global__ void k_add_partials(const double* partials, int k, double* totals) {
 
 // -------------------------------------------------------------- launchers --
 template <typename R, typename G> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value)
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_theta_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 grid(tiles, tiles, a.count);
     k_theta<R, G><<<grid, 256, 0, s>>>(a);
@@ -673,6 +681,8 @@ template <typename R, typename G> cudaError_t launch_gamma(const LayerArgs<R>& a
     k_gamma_direct<R, G><<<g1, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<R, float>::value)
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_gamma_gemm_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 g2(tiles, tiles, 2 * a.count);
     k_gamma_gemm<R, G><<<g2, 256, 0, s>>>(a);
@@ -685,6 +695,8 @@ template <typename R, typename G> cudaError_t launch_xform(const LayerArgs<R>& a
     return cudaGetLastError();
 }
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value)
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_proj_tc(a, s);
     dim3 grid((2 * a.chip + 31) / 32, (a.chip + 31) / 32, a.count);
     k_proj<R><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(NB * 32, 1) k_orth(LayerArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int j = blockIdx.x;
     const int32_t* d = A.dims + j * kDims;
-    if (A.refine && d[D_REFINE] != 1) return;  // the FP64 resolution runs only undecided bonds
+    if (A.refine == 1 && d[D_REFINE] != 1) return;  // the FP64 resolution runs only undecided bonds
     const int rows = 2 * d[D_CL];
     const int cols = d[D_CM];
     C* W = A.w + (size_t)j * A.ldw * A.ldw;

@@ -31,6 +31,7 @@ __all__ = [
     "gates_to_interleaved",
     "saturated_bond",
     "trotter_heisenberg_circuit",
+    "random_mps_scaled",
 ]
 
 
@@ -76,6 +77,17 @@ def random_mps_tensors(seed: int, n_sites: int, chi: int, d: int = 2):
     for s in range(n_sites):
         shape = (d, dims[s], dims[s + 1])
         out.append(rng.uniform(-1.0, 1.0, shape) + 1j * rng.uniform(-1.0, 1.0, shape))
+    return out
+
+
+def random_mps_scaled(seed: int, n_sites: int, chi: int, d: int = 2):
+    """The random tensors of random_mps_tensors, each scaled to the Frobenius
+    norm sqrt(chi_right) that a canonical (left-orthonormal) tensor has, so that
+    the norm of a long random MPS stays within floating-point range (it would
+    otherwise grow geometrically with N)."""
+    out = []
+    for m in random_mps_tensors(seed, n_sites, chi, d):
+        out.append(m * (np.sqrt(m.shape[2]) / np.linalg.norm(m)))
     return out
 
 

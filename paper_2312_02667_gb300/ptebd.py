@@ -38,7 +38,9 @@ EXPORTS = (
     "ptebd_work_counters", "ptebd_svd_workspace_bytes", "ptebd_svd_batched",
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
-    "ptebd_set_chunk_streams", "ptebd_test_wait_timeout", "ptebd_alu_peak",
+    "ptebd_set_chunk_streams", "ptebd_test_wait_timeout", "ptebd_alu_peak", "ptebd_set_regauge_precision",
+    "ptebd_set_jacobi_width", "ptebd_autotune", "ptebd_set_tensor_cores",
+    "ptebd_set_svd_polish",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor", "resolve")
 
@@ -103,6 +105,11 @@ _SIGS = {
     "ptebd_set_chunk_streams": (_P, ctypes.c_int32),
     "ptebd_test_wait_timeout": (_P, ctypes.c_int32),
     "ptebd_alu_peak": (ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P, _D, _D),
+    "ptebd_set_regauge_precision": (_P, ctypes.c_int32),
+    "ptebd_set_jacobi_width": (_P, ctypes.c_int32),
+    "ptebd_set_tensor_cores": (_P, ctypes.c_int32),
+    "ptebd_set_svd_polish": (_P, ctypes.c_int32),
+    "ptebd_autotune": (_P, _D, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _D),
 }
 
 
@@ -319,6 +326,30 @@ def ptebd_sample(h, uniforms, workspace=None) -> np.ndarray:
 
 def ptebd_set_chunk_streams(h, n):
     _check(lib.ptebd_set_chunk_streams(h, int(n)), h)
+
+
+def ptebd_set_regauge_precision(h, precision):
+    _check(lib.ptebd_set_regauge_precision(h, PTEBD_FP64 if precision == "fp64" else PTEBD_MIXED), h)
+
+
+def ptebd_set_svd_polish(h, mode):
+    _check(lib.ptebd_set_svd_polish(h, int(mode)), h)
+
+
+def ptebd_set_tensor_cores(h, enable):
+    _check(lib.ptebd_set_tensor_cores(h, 1 if enable else 0), h)
+
+
+def ptebd_set_jacobi_width(h, nw):
+    _check(lib.ptebd_set_jacobi_width(h, int(nw)), h)
+
+
+def ptebd_autotune(h, gates, parity, scratch_ptr, scratch_bytes):
+    """(block width, chunks, best ms, ms of the previous configuration)."""
+    ptr, on_dev, keep = _gates_arg(gates)
+    best = np.zeros(4)
+    _check(lib.ptebd_autotune(h, ptr, int(parity), on_dev, _P(scratch_ptr), int(scratch_bytes), _dptr(best)), h)
+    return int(best[0]), int(best[1]), float(best[2]), float(best[3])
 
 
 def ptebd_test_wait_timeout(h, enable):
@@ -576,6 +607,25 @@ class State:
 
     def work_counters(self):
         return ptebd_work_counters(self.handle)
+
+    def set_regauge_precision(self, precision):
+        ptebd_set_regauge_precision(self.handle, precision)
+
+    def set_jacobi_width(self, nw):
+        ptebd_set_jacobi_width(self.handle, nw)
+
+    def set_tensor_cores(self, enable):
+        ptebd_set_tensor_cores(self.handle, enable)
+
+    def set_svd_polish(self, mode):
+        ptebd_set_svd_polish(self.handle, mode)
+
+    def autotune(self, gates, parity):
+        """Tune the launch configuration on this state's next layer (the state is
+        left unchanged); scratch of state_bytes from the caching allocator."""
+        import torch
+        scratch = torch.empty(self._state_buf.numel(), dtype=torch.uint8, device=self.device)
+        return ptebd_autotune(self.handle, gates, parity, scratch.data_ptr(), scratch.numel())
 
     def export(self):
         """(gammas, lambdas) as complex128 / float64 numpy arrays."""

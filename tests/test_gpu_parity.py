@@ -164,6 +164,35 @@ def test_ptsu_parity_and_theorem_4(ptebd, prec):
     assert c < floor, (c, floor)
 
 
+def test_fp64_regauge_of_a_mixed_state(ptebd):
+    # The PtSU steps of a complex64 state run in FP64 (ptebd_set_regauge_precision):
+    # each tSU is the FP64 computation on the stored complex64 Gamma, so one step
+    # matches the oracle to FP32-rounding level, and after N/2 steps (Theorem 4)
+    # the distance to canonical form is limited only by the complex64 storage of
+    # Gamma: |sum A^dag A - I|_F <= about 2 u chi (u = 2^-24), far below the
+    # complex64 Jacobi's floor of the test above.
+    n, chi = 12, 16
+    mps = oracle.canonicalize(inputs.random_mps_tensors(5, n, 16))
+    cut = oracle.scale_to_unit_norm(oracle.truncate_all_bonds(mps, 8))
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-14)
+    st.set_regauge_precision("fp64")
+    load_into(st, cut)
+    ref = cut.copy()
+    w0 = st.work_counters()
+    st.regauge(1)
+    oracle.ptsu_step(ref, chi, 1e-14)
+    got = to_oracle(st)
+    assert st.work_counters()[8] - w0[8] == n - 1  # every tSU bond ran in FP64
+    for b in range(n - 1):
+        compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-6, 1e-14, chi)
+    assert fidelity(got, cut) >= 1 - 1e-9
+    st.regauge(n // 2 - 1)
+    c = oracle.distance_to_canonical(to_oracle(st))
+    floor = 4 * chi * 2.0 ** -24
+    print(f"C after N/2 FP64 PtSU steps of a complex64 state: {c:.2e} (bound {floor:.2e})")
+    assert c < floor, (c, floor)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_layer_with_ptsu_g1(ptebd, prec):
     n, chi = 40, 16

@@ -122,3 +122,27 @@ def test_structural_rank_decides_cz_layers_in_complex64(ptebd):
     resolved = st.work_counters()[8]
     print(f"RQC-1D (CZ): {resolved} of {gated} gated bond updates resolved in FP64")
     assert resolved < gated // 4
+
+
+def test_resolution_inside_batch_graphs(ptebd):
+    # In the batch graphs the FP64 pass is an IF node switched on by the
+    # complex64 truncation; states run there must be bit-identical to the same
+    # states run one by one (FP64 pass launched directly), with the same
+    # number of bonds recomputed in FP64, which must not be zero here
+    n, chi, depth, dt = 20, 32, 12, 0.1
+    circuits = [inputs.trotter_heisenberg_circuit(20 + i, n, depth, dt) for i in range(3)]
+    solo = [ptebd.State(n, chi, "mixed", cutoff=CUT) for _ in circuits]
+    for st, circ in zip(solo, circuits):
+        for parity, bonds, gates in circ:
+            st.apply_layer(gates, parity)
+    batched = [ptebd.State(n, chi, "mixed", cutoff=CUT) for _ in circuits]
+    batch = ptebd.Batch(batched)
+    for layer in range(depth):
+        batch.apply_layer([c[layer][2] for c in circuits], [c[layer][0] for c in circuits])
+    batch.close()
+    for a, b in zip(solo, batched):
+        ga, la = a.export()
+        gb, lb = b.export()
+        assert all(np.array_equal(x, y) for x, y in zip(ga, gb))
+        assert all(np.array_equal(x, y) for x, y in zip(la, lb))
+        assert a.work_counters()[8] == b.work_counters()[8] > 0

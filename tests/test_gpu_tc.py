@@ -1,0 +1,64 @@
+"""The two-site tensor of a complex64 state on the tensor cores (tcgen05
+kind::tf32, 3xTF32 split) against the same layer with theta' formed by FP32
+FMAs on the CUDA cores, and both against the oracle (Sec. II C's theta =
+Lambda Gamma Lambda Gamma Lambda and theta' = U theta).  FP32 accuracy is what
+the split must keep: the layers agree to the mixed path's tolerances, far
+inside what one TF32 product (1e-3 relative) would allow."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02667_gb300 import inputs
+
+from gpu_helpers import compare_spectra, fidelity, load_into, mini_vidal, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptebd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_02667_gb300 import ptebd as mod
+    return mod
+
+
+@pytest.mark.parametrize("chi,g", [(64, 0), (128, 1)])
+def test_tensor_core_layers_match_cuda_cores_and_oracle(ptebd, chi, g):
+    n, depth = 24, 12
+    circuit = inputs.brickwork_circuit(51, n, depth)
+    ref = oracle.product_state(n)
+    tc = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=g)
+    cc = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=g)
+    cc.set_tensor_cores(False)
+    worst = 0.0
+    for layer, (parity, bonds, gates) in enumerate(circuit):
+        load_into(tc, ref)
+        load_into(cc, ref)
+        tc.apply_layer(gates, parity)
+        cc.apply_layer(gates, parity)
+        oracle.apply_layer(ref, gates, parity, chi, 1e-12, g=g)
+        a, b = to_oracle(tc), to_oracle(cc)
+        for bb in range(n - 1):
+            worst = max(worst, compare_spectra(a.lambdas[bb], ref.lambdas[bb], 1e-5, 1e-12, chi))
+            compare_spectra(a.lambdas[bb], b.lambdas[bb], 1e-5, 1e-12, chi)
+        assert fidelity(a, ref) >= 1 - 1e-6, layer
+        assert fidelity(a, b) >= 1 - 1e-6, layer
+    print(f"chi {chi}: tensor-core layers, worst normwise deviation from the oracle {worst:.2e}")
+
+
+def test_tensor_core_sampled_bonds_chi256(ptebd):
+    # saturated chi = 256 environments (theta' 512 x 512, a 4 x 4 grid of
+    # tiles per bond): single-bond updates against the oracle
+    chi = 256
+    for j in range(3):
+        env = inputs.saturated_bond(700 + j, chi)
+        mini = mini_vidal(env["lam_l"], env["gamma_l"], env["lam_c"], env["gamma_r"], env["lam_r"])
+        ms = ptebd.State(4, chi, "mixed", cutoff=1e-12)
+        load_into(ms, mini)
+        ms.apply_bonds(np.array([1], np.int32), env["gate"][None])
+        got = to_oracle(ms)
+        oracle.update_bond(mini, 1, env["gate"], chi, 1e-12)
+        compare_spectra(got.lambdas[1], mini.lambdas[1], 1e-5, 1e-12, chi)
+        ms.close()

@@ -1,0 +1,81 @@
+"""The autotuner and the Jacobi block width on the GPU (launch choices of the
+library; the paper has no counterpart).  Tuning times candidates on the state's
+own next layer and must leave the state exactly as it was; every width must
+give the oracle's layer; a given width is bit-identical run to run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02667_gb300 import inputs
+
+from gpu_helpers import compare_spectra, fidelity, load_into, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ptebd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_02667_gb300 import ptebd as mod
+    return mod
+
+
+def snapshot(st):
+    gam, lam = st.export()
+    return [g.copy() for g in gam], [l.copy() for l in lam]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_autotune_leaves_the_state_unchanged(ptebd, prec):
+    n, chi, depth = 64, 32, 8
+    st = ptebd.State(n, chi, prec, cutoff=1e-12, g=1)
+    circuit = inputs.brickwork_circuit(41, n, depth + 1)
+    for parity, bonds, gates in circuit[:depth]:
+        st.apply_layer(gates, parity)
+    gam0, lam0 = snapshot(st)
+    w0 = st.work_counters()
+    _, layers0 = st.svd_sweeps()
+    nw, chunks, best_ms, prev_ms = st.autotune(circuit[depth][2], circuit[depth][0])
+    gam1, lam1 = snapshot(st)
+    assert all(np.array_equal(a, b) for a, b in zip(gam0, gam1))
+    assert all(np.array_equal(a, b) for a, b in zip(lam0, lam1))
+    assert st.work_counters() == w0 and st.svd_sweeps()[1] == layers0
+    assert nw in ((8, 16) if prec == "mixed" else (8,)) and chunks >= 1 and 0 < best_ms
+    assert prev_ms < 0 or best_ms <= prev_ms
+    # the tuned handle then runs that layer as the oracle does
+    ref = to_oracle(st)
+    parity, bonds, gates = circuit[depth]
+    st.apply_layer(gates, parity)
+    oracle.apply_layer(ref, gates, parity, chi, 1e-12, g=1)
+    got = to_oracle(st)
+    for b in range(n - 1):
+        compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-10 if prec == "fp64" else 1e-5, 1e-12, chi)
+    assert fidelity(got, ref) >= 1 - (1e-9 if prec == "fp64" else 1e-6)
+    print(f"{prec}: tuned width {nw}, chunks {chunks}: {best_ms:.2f} ms (before: {prev_ms:.2f} ms)")
+
+
+@pytest.mark.parametrize("nw", [8, 16])
+def test_jacobi_width_matches_oracle_and_repeats_bitwise(ptebd, nw):
+    n, chi, depth = 32, 64, 8
+    circuit = inputs.brickwork_circuit(43, n, depth)
+    ref = oracle.product_state(n)
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-12)
+    st.set_jacobi_width(nw)
+    for parity, bonds, gates in circuit:
+        load_into(st, ref)
+        st.apply_layer(gates, parity)
+        oracle.apply_layer(ref, gates, parity, chi, 1e-12)
+        got = to_oracle(st)
+        for b in bonds:
+            compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-5, 1e-12, chi)
+        assert fidelity(got, ref) >= 1 - 1e-6
+    runs = []
+    for _ in range(2):
+        st.reset()
+        for parity, bonds, gates in circuit:
+            st.apply_layer(gates, parity)
+        runs.append(snapshot(st))
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0][0], runs[1][0]))
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))

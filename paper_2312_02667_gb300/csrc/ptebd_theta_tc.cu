@@ -14,14 +14,20 @@
 // Complex arithmetic on the real tensor cores: with the real and imaginary
 // parts of X interleaved along K (the complex64 storage order), the real part
 // of theta is X' B_re^T and the imaginary part X' B_im^T, where row n of
-// B_re holds (Re Y, -Im Y) and row n of B_im holds (Im Y, Re Y) pairwise.  Two
-// FP32 accumulators of 128 x 128 in tensor memory (256 columns).
+// B_re holds (Re Y, -Im Y) and row n of B_im holds (Im Y, Re Y) pairwise.
 //
 // 3xTF32: every operand value v is split into hi = v rounded to TF32 and
 // lo = v - hi (exact in FP32); a product is accumulated as
 // hi*hi + hi*lo + lo*hi, leaving out lo*lo (about 2^-22 relative) - FP32
 // accuracy, which the mixed path needs (a single TF32 product changes
-// theta by 1e-3 relative).
+// theta by 1e-3 relative).  The hi*hi products go to one FP32 accumulator and
+// the two cross terms to a second one, added in the epilogue: the tensor
+// cores' FP32 accumulation does not round to nearest (measured on GB300 it
+// shrinks every sum by about 2.5e-8 relative per MMA, always in the same
+// direction), and a separate accumulator of the small cross terms keeps that
+// shrinkage of the large hi*hi sum from being applied again to every term.
+// Four accumulators of 128 x 128 FP32 (real, imaginary, and their
+// corrections): all 512 columns of tensor memory.
 //
 // Operands are staged by all threads into shared memory in the K-major,
 // 128-byte-swizzled layout that the MMA descriptors describe (rows of 32 FP32
@@ -182,14 +188,14 @@ __device__ __forceinline__ void put_b(unsigned char* S, int n, int kk, float2 br
     *reinterpret_cast<float2*>(S + 5 * kTile + o) = make_float2(l2, l3);
 }
 
-// Barriers and tensor memory of a CTA (256 columns: the two accumulators).
+// Barriers and tensor memory of a CTA (512 columns: the four accumulators).
 __device__ __forceinline__ uint32_t tc_begin(uint64_t* bar, uint32_t* tmem_slot) {
     if (threadIdx.x == 0) {
         tc_mbar_init(&bar[0], 1);
         tc_mbar_init(&bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, 256);
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(tmem_slot, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -198,7 +204,7 @@ __device__ __forceinline__ uint32_t tc_begin(uint64_t* bar, uint32_t* tmem_slot)
 __device__ __forceinline__ void tc_end(uint32_t tmem) {
     tc_fence_before();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 256);
+    if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 512);
 }
 
 // The MMA pipeline of one CTA over nk K chunks of 16 complex values, two
@@ -208,12 +214,14 @@ __device__ __forceinline__ void tc_end(uint32_t tmem) {
 // of chunk kc + 1 is issued before the MMAs of chunk kc and before the wait
 // for the stage it will fill, so its memory latency overlaps the tensor-core
 // work.  One thread issues the chunk's 24 MMAs (3xTF32 for the real and the
-// imaginary accumulator, 4 K steps of 8 FP32 values) and commits them to the
+// imaginary part, 4 K steps of 8 FP32 values: hi*hi into the accumulators at
+// columns 0 and 128, the cross terms into the corrections at 256 and 384) and
+// commits them to the
 // stage's mbarrier, which the threads wait on before they refill that stage.
 // Returns false when a wait ran out (the accumulators cannot be trusted then).
 template <typename Fetch, typename Put>
 __device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int nk, Fetch&& fetch, Put&& put) {
-    const uint32_t d_re = tmem, d_im = tmem + 128;
+    const uint32_t d_re = tmem, d_im = tmem + 128, c_re = tmem + 256, c_im = tmem + 384;
     float2 ra[8], rb[8];
     if (nk > 0) fetch(0, ra, rb);
     bool ok = true;
@@ -237,11 +245,11 @@ __device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int
                 const uint64_t ih = sdesc_sw128(base + 4 * kTile + off), il = sdesc_sw128(base + 5 * kTile + off);
                 const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
                 mma_tf32(d_re, ah, rh, kIdesc, acc);
-                mma_tf32(d_re, ah, rl, kIdesc, 1u);
-                mma_tf32(d_re, al, rh, kIdesc, 1u);
+                mma_tf32(c_re, ah, rl, kIdesc, acc);
+                mma_tf32(c_re, al, rh, kIdesc, 1u);
                 mma_tf32(d_im, ah, ih, kIdesc, acc);
-                mma_tf32(d_im, ah, il, kIdesc, 1u);
-                mma_tf32(d_im, al, ih, kIdesc, 1u);
+                mma_tf32(c_im, ah, il, kIdesc, acc);
+                mma_tf32(c_im, al, ih, kIdesc, 1u);
             }
             mma_commit(&bar[st]);
         }
@@ -365,10 +373,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(LayerArgs<float> a) 
         float* dst = half ? th_im : th_re;
 #pragma unroll 1
         for (int c0 = 0; c0 < 128; c0 += 16) {
-            float v[16];
+            float v[16], c[16];
             tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 128 + c0), v);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 + half * 128 + c0), c);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dst[(c0 + i) * kThPitch + row] = v[i];
+            for (int i = 0; i < 16; ++i) dst[(c0 + i) * kThPitch + row] = v[i] + c[i];
         }
     }
     tc_end(tmem);
@@ -536,9 +545,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gamma_tc(LayerArgs<float> a) 
 #pragma unroll 1
         for (int cc = 0; cc < 64; cc += 16) {
             const int cl0 = half * 64 + cc;
-            float vre[16], vim[16];
+            float vre[16], vim[16], cre[16], cim[16];
             tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cl0, vre);
             tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128u + (uint32_t)cl0, vim);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256u + (uint32_t)cl0, cre);
+            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 384u + (uint32_t)cl0, cim);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                vre[i] += cre[i];
+                vim[i] += cim[i];
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 const int col = c0 + cl0 + i;
@@ -557,103 +573,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gamma_tc(LayerArgs<float> a) 
     tc_end(tmem);
 }
 
-// ---------------------------------------------------------- tSU projection --
-// M^dag = theta^dag U_X (the second tSU matrix, Sec. III D), the product of
-// k_proj on the tensor cores: out[r, c] = sum_k A[r, k] B[k, c] / sigma_X[c]
-// with A = theta^dag (rows 2 chi_{b+1}, K = 2 chi_{b-1}) in w0 and B = U_X
-// Sigma_X (K x chi_b) in w; a zero sigma_X gives a zero column.  A CTA computes
-// a 128 x 128 tile of out (w1), written straight from tensor memory.
-// grid (ceil(2 chip / 128), ceil(chip / 128), count), 256 threads, kTcSmem bytes.
-__global__ void __launch_bounds__(kTcThreads, 1) k_proj_tc(LayerArgs<float> a) {
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);  // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
-    float* bscl = reinterpret_cast<float*>(sm + 2 * kStage + 64);  // [128]
-
-    const int j = blockIdx.z;
-    const int32_t* d = a.dims + j * kDims;
-    const int cl = d[D_CL], cm = d[D_CM], cr = d[D_CR];
-    const int rows = 2 * cr, kdim = 2 * cl;
-    const int r0 = blockIdx.x * 128, c0 = blockIdx.y * 128;
-    if (r0 >= rows || c0 >= cm) return;
-    const size_t ldw = a.ldw;
-    const float2* A = a.w0 + (size_t)j * ldw * ldw;
-    const float2* B = a.w + (size_t)j * ldw * ldw;
-    float2* out = a.w1 + (size_t)j * ldw * ldw;
-    const double* sig = a.norms + (size_t)j * ldw;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid < 128) {
-        const int gc = c0 + tid;
-        const double sg = gc < cm ? sig[gc] : 0.0;
-        bscl[tid] = sg > 0.0 ? (float)(1.0 / sg) : 0.f;
-    }
-    const uint32_t tmem = tc_begin(bar, tmem_slot);
-    const int nk = (kdim + 15) / 16;
-    // element i of a thread: A (row e & 127 = output row, kk = e >> 7), B (kk = e & 15, row e >> 4), e = tid + 256 i
-    const bool ok = tc_pipeline(
-        sm, bar, tmem, nk,
-        [&](int kc, float2 (&ra)[8], float2 (&rb)[8]) {
-            float2 xb[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int e = tid + kTcThreads * i;
-                const int gr = r0 + (e & 127), gk = kc * 16 + (e >> 7);
-                ra[i] = (gr < rows && gk < kdim) ? A[(size_t)gk * ldw + gr] : make_float2(0.f, 0.f);
-                const int gc = c0 + (e >> 4), gk2 = kc * 16 + (e & 15);
-                xb[i] = (gc < cm && gk2 < kdim) ? B[(size_t)gc * ldw + gk2] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int c = (tid + kTcThreads * i) >> 4;
-                rb[i] = make_float2(xb[i].x * bscl[c], xb[i].y * bscl[c]);
-            }
-        },
-        [&](unsigned char* S, const float2 (&ra)[8], const float2 (&rb)[8]) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {  // A B: B_re rows (Re b, -Im b), B_im rows (Im b, Re b)
-                const int e = tid + kTcThreads * i;
-                put_a(S, e & 127, e >> 7, ra[i]);
-                put_b(S, e >> 4, e & 15, make_float2(rb[i].x, -rb[i].y), make_float2(rb[i].y, rb[i].x));
-            }
-        });
-    if (!ok) {
-        if (tid == 0) atomicOr(a.err, DERR_TIMEOUT | DERR_DRAIN);
-        tc_end(tmem);
-        return;
-    }
-    {
-        const int q = warp & 3, half = warp >> 2;
-        const int gr = r0 + 32 * q + lane;
-#pragma unroll 1
-        for (int cc = 0; cc < 64; cc += 16) {
-            const int cl0 = half * 64 + cc;
-            float vre[16], vim[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cl0, vre);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128u + (uint32_t)cl0, vim);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int gc = c0 + cl0 + i;
-                if (gr < rows && gc < cm) out[(size_t)gc * ldw + gr] = make_float2(vre[i], vim[i]);
-            }
-        }
-    }
-    tc_end(tmem);
-}
-
 }  // namespace
 
 cudaError_t theta_tc_prepare() {
     cudaError_t e = cudaFuncSetAttribute(k_theta_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gamma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     return e;
-}
-
-cudaError_t launch_proj_tc(const LayerArgs<float>& a, cudaStream_t s) {
-    dim3 grid((2 * a.chip + 127) / 128, (a.chip + 127) / 128, a.count);
-    k_proj_tc<<<grid, kTcThreads, kTcSmem, s>>>(a);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_gamma_gemm_tc(const LayerArgs<float>& a, cudaStream_t s) {

@@ -353,17 +353,11 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": "c64" if args.precision == "mixed" else "c128",
         "data": "synthetic",
-        "config": {
-            "workload": (f"1D brickwork circuit of Haar-random U(4) gates, N={n}, chi_max={chi}, cutoff 1e-12, "
-                         f"{args.precision} precision, PtSU g={args.g} after every layer; a step = one gate layer "
-                         f"+ its PtSU step on a state saturated at chi_max"),
-            "n_sites": n, "chi_max": chi, "precision": args.precision, "g": args.g,
-            "prefill_layers": args.prefill, "max_chi_at_start": int(chi_now.max()),
-            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (Gamma store and theta workspace are GiB-sized; no flush needed)",
-            "gated_bonds_per_step": gated / args.steps,
-            "tsu_bonds_per_step": args.g * (n - 1),
-        },
+        "config": headline_config(args, world),
+        "precision": args.precision,
+        "prefill_layers": args.prefill, "max_chi_at_start": int(chi_now.max()),
+        "gated_bonds_per_step": gated / args.steps,
+        "tsu_bonds_per_step": args.g * (n - 1),
         "chunk_streams": n_chunks,
         "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},
         "kernels_note": ("per-kernel CUDA-event times from a separate pass of the next two layers on one stream "
@@ -499,6 +493,18 @@ def fp64_at_headline(args, st, circuit, layer, local_rank):
 
 
 # ------------------------------------------------------------- reference --
+def headline_config(args, world):
+    """The workload of the headline line, the same for both arms."""
+    return {
+        "workload": (f"1D brickwork circuit of Haar-random U(4) gates, N={args.n_sites}, chi_max={args.chi}, "
+                     f"cutoff 1e-12, PtSU g={args.g} after every layer; a step = one gate layer + its PtSU "
+                     f"step on a state saturated at chi_max"),
+        "n_sites": args.n_sites, "chi_max": args.chi, "g": args.g,
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        "l2": "inputs larger than L2 (Gamma store and theta workspace are GiB-sized; no flush needed)",
+    }
+
+
 def run_reference(args):
     """The oracle on the host cores, one bounded sample per step."""
     per_step = max(4, args.cpu_sample // 4)
@@ -515,9 +521,7 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": (f"1D brickwork circuit of Haar-random U(4) gates, N={args.n_sites}, "
-                                f"chi_max={args.chi}, cutoff 1e-12, PtSU g={args.g}; oracle sample per step"),
-                   "n_sites": args.n_sites, "chi_max": args.chi, "g": args.g},
+        "config": headline_config(args, args.gpus),
         "impl": "reference",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -631,9 +635,9 @@ def serving_bench(args):
                         if p_ >= 0:
                             st.apply_layer(g_, p_)
         first, _ = _timed_run(reset, body)
-        w0 = [st.work_counters()[8] for st in states]
         wall, dev = _timed_run(reset, body)
-        resolved = sum(st.work_counters()[8] - a for st, a in zip(states, w0))
+        # ptebd_reset clears the work counters: these are the timed pass's own
+        resolved = sum(st.work_counters()[8] for st in states)
         if batch is not None:
             batch.close()
         return first, wall, dev, resolved
@@ -754,14 +758,13 @@ def qft_bench(args):
             st.apply_bonds(bonds, us)
 
     first, _ = _timed_run(reset, body)
-    w0 = st.work_counters()
     wall, dev = _timed_run(reset, body)
-    w1 = st.work_counters()
+    w1 = st.work_counters()  # the timed pass's own (ptebd_reset clears them)
     return {"metric": "QFT on a random MPS, N=96, chi 64 (App. B workload)", "unit": "bond-SVDs/s",
             "value": gated / wall, "higher_is_better": True, "n_gpus": 1, "dtype": "c64", "data": "synthetic",
             "ms_per_compiled_layer": 1e3 * wall / len(layers), "compiled_layers": len(layers),
             "gated_bond_updates": gated, "wall_s": wall, "device_s": dev, "first_pass_s": first,
-            "max_chi": int(max(st.chi())), "fp64_resolved_bonds": w1[8] - w0[8],
+            "max_chi": int(max(st.chi())), "fp64_resolved_bonds": w1[8],
             "config": {"workload": "QFT compiled onto the line by the library's SWAP network (2N-3 layers, "
                                    "N(N-1)/2 gates) on a canonicalised random MPS of bond dimension 10, N=96, "
                                    "chi_max 64, cutoff 1e-12, mixed, g = 0", "seed": 96}}

@@ -92,6 +92,8 @@ def parse():
                    help="--serving: advance the states one by one (no batch graph), for comparison")
     p.add_argument("--no-tensor-cores", action="store_true",
                    help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
+    p.add_argument("--jacobi-width", type=int, default=0, choices=[0, 8, 16],
+                   help="complex64 Jacobi block width (0: the library's choice)")
     p.add_argument("--resolve", type=float, default=-1.0,
                    help="mixed: the level below which complex64 singular values are resolved in FP64 (-1: default)")
     p.add_argument("--qft", action="store_true",
@@ -230,6 +232,8 @@ def run_ours(args, rank, world, local_rank):
         st.set_tensor_cores(False)
     if args.chunk_streams:
         st.set_chunk_streams(args.chunk_streams)
+    if args.jacobi_width:
+        st.set_jacobi_width(args.jacobi_width)
     n_layers = args.prefill + args.warmup + args.steps
     diag_layers = 2
     circuit = inputs.brickwork_circuit(7 + rank, n, n_layers + diag_layers + args.steps + 2)
@@ -359,6 +363,7 @@ def run_ours(args, rank, world, local_rank):
         "gated_bonds_per_step": gated / args.steps,
         "tsu_bonds_per_step": args.g * (n - 1),
         "chunk_streams": n_chunks,
+        "jacobi_width": args.jacobi_width or "library choice",
         "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},
         "kernels_note": ("per-kernel CUDA-event times from a separate pass of the next two layers on one stream "
                          "(events around every launch serialise the chunks); the timed steps run the chunks "

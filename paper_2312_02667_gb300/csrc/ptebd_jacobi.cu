@@ -813,8 +813,14 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     }
 }
 
+// CTAs per SM the register allocation is held to: the complex64 kernel with
+// 8-column blocks (106 KB of shared memory at 512 rows) runs two CTAs per SM,
+// 16 warps as with one 16-column CTA, on two independent bonds.
+template <typename R, int NW> struct JacobiMinBlocks { static constexpr int v = 1; };
+template <> struct JacobiMinBlocks<float, 8> { static constexpr int v = 2; };
+
 template <typename R, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) k_jacobi(LayerArgs<R> A) {
+__global__ void __launch_bounds__(NW * 32, JacobiMinBlocks<R, NW>::v) k_jacobi(LayerArgs<R> A) {
     using C = cx_t<R>;
     extern __shared__ __align__(128) unsigned char smem[];
     const int j = blockIdx.x;
@@ -871,9 +877,10 @@ template <typename R> cudaError_t jacobi_prepare() {
     constexpr int NW = JacobiNW<R>::v;
     cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, NW));
-    if (e == cudaSuccess && std::is_same<R, float>::value)
-        e = cudaFuncSetAttribute(k_jacobi<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, 8));
+    if constexpr (std::is_same<R, float>::value)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_jacobi<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, 8));
     return e;
 }
 
@@ -881,10 +888,14 @@ template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStrea
     const int prec = std::is_same<R, double>::value ? PTEBD_FP64 : PTEBD_MIXED;
     const int nw = jacobi_block_width(prec, a.nw);
     const size_t smem = jacobi_smem_bytes(prec, a.ldw, nw);
-    if (nw == 8)
-        k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);
-    else
-        k_jacobi<R, 16><<<a.count, 16 * 32, smem, s>>>(a);
+    if constexpr (std::is_same<R, double>::value) {
+        k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);  // complex128: 8-column blocks only
+    } else {
+        if (nw == 8)
+            k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);
+        else
+            k_jacobi<R, 16><<<a.count, 16 * 32, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -94,6 +94,8 @@ def parse():
                    help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
     p.add_argument("--jacobi-width", type=int, default=0, choices=[0, 8, 16],
                    help="complex64 Jacobi block width (0: the library's choice)")
+    p.add_argument("--jacobi-pairs", type=int, default=0, choices=[0, 1, 2],
+                   help="complex64 Jacobi I columns per warp at width 16 (0: the library's choice)")
     p.add_argument("--resolve", type=float, default=-1.0,
                    help="mixed: the level below which complex64 singular values are resolved in FP64 (-1: default)")
     p.add_argument("--qft", action="store_true",
@@ -234,6 +236,8 @@ def run_ours(args, rank, world, local_rank):
         st.set_chunk_streams(args.chunk_streams)
     if args.jacobi_width:
         st.set_jacobi_width(args.jacobi_width)
+    if args.jacobi_pairs:
+        st.set_jacobi_pairs(args.jacobi_pairs)
     n_layers = args.prefill + args.warmup + args.steps
     diag_layers = 2
     circuit = inputs.brickwork_circuit(7 + rank, n, n_layers + diag_layers + args.steps + 2)
@@ -364,6 +368,7 @@ def run_ours(args, rank, world, local_rank):
         "tsu_bonds_per_step": args.g * (n - 1),
         "chunk_streams": n_chunks,
         "jacobi_width": args.jacobi_width or "library choice",
+        "jacobi_columns_per_warp": args.jacobi_pairs or "library choice",
         "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},
         "kernels_note": ("per-kernel CUDA-event times from a separate pass of the next two layers on one stream "
                          "(events around every launch serialise the chunks); the timed steps run the chunks "
@@ -673,8 +678,9 @@ def serving_bench(args):
         choices[kk] = st.autotune(gates, parity)
     tune_s = time.perf_counter() - t0
     for i, st in enumerate(states):
-        nw, chunks, _, _ = choices[key(i)]
+        nw, chunks, _, _, pairs = choices[key(i)]
         st.set_jacobi_width(nw)
+        st.set_jacobi_pairs(pairs)
         st.set_chunk_streams(chunks)
     first_t, wall_t, dev_t, _ = run_pass()
     for st in states:
@@ -685,7 +691,7 @@ def serving_bench(args):
             "untuned": {"value": gated / wall_u, "wall_s": wall_u, "device_s": dev_u, "first_pass_s": first_u},
             "tuned": {"value": gated / wall_t, "wall_s": wall_t, "device_s": dev_t, "first_pass_s": first_t,
                       "tuning_s": tune_s,
-                      "choices": {f"chi{a}_nbits{b}": {"jacobi_width": c[0], "chunks": c[1]}
+                      "choices": {f"chi{a}_nbits{b}": {"jacobi_width": c[0], "chunks": c[1], "columns_per_warp": c[4]}
                                   for (a, b), c in choices.items()}},
             "circuit_layers_per_s": float(ds.sum()) / wall_t, "batch_layers_per_s": len(layers) / wall_t,
             "gated_bond_updates": gated, "fp64_resolved_bonds": resolved,

@@ -212,10 +212,20 @@ int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable);
  * the SVD's accuracy). */
 int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw);
 
+/* Columns of the complex64 Jacobi register block per warp at block width 16
+ * (no counterpart in the paper: a scheduling choice).  pairs = 1 (the
+ * default): 16 warps, one I column each, one column pair a round; pairs = 2:
+ * 8 warps, each holding two I columns and rotating two independent column
+ * pairs a round with their instruction streams interleaved.  The same pairs
+ * meet in the same order (bit-identical results to pairs = 1); width 8 and
+ * complex128 ignore it.  PTEBD_ERR_INVALID for other values. */
+int ptebd_set_jacobi_pairs(ptebd_state* st, int32_t pairs);
+
 /* Autotuner (no counterpart in the paper: a scheduling choice of the library).
  * Times every candidate launch configuration on the state's own next layer
  * (the gates and parity a ptebd_apply_layer call would get, with the config's
- * PtSU steps): Jacobi block width (complex64: 16 and 8) x bond chunks (1, 2,
+ * PtSU steps): Jacobi block width and columns per warp (complex64: 16 with
+ * one or two, 8 with one) x bond chunks (1, 2,
  * 4, 8, 12, 16, those the workspace can run concurrently); each candidate runs
  * twice from the saved state and the second run is timed with CUDA events on
  * the handle's stream.  The state is copied into `scratch` (device memory,
@@ -224,9 +234,10 @@ int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw);
  * leaves the state, its counters and its layer count as it found them.  The
  * fastest configuration is set on the handle and remembered for the process
  * under (chi_max padded, precision, bit length of N - 1, g): later
- * ptebd_create calls with the same key start with it.  best (may be NULL):
- * [block width, chunks, ms of the best, ms of the configuration the handle
- * had (-1 if it was not among the candidates)].  Synchronous. */
+ * ptebd_create calls with the same key start with it.  best (may be NULL, else
+ * 5 doubles): [block width, chunks, ms of the best, ms of the configuration
+ * the handle had (-1 if it was not among the candidates), columns per warp].
+ * Synchronous. */
 int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t gates_on_device,
                    void* scratch, size_t scratch_bytes, double* best);
 

@@ -47,6 +47,7 @@ struct ptebd_state {
     int wait_test = 0;      // see ptebd_test_wait_timeout
     bool regauge64 = false; // PTEBD_MIXED: tSU stages run in FP64 (ptebd_set_regauge_precision)
     int jacobi_nw = 0;      // Jacobi block width (0: default; see ptebd_set_jacobi_width)
+    int jacobi_pairs = 1;   // I columns per warp at width 16 (ptebd_set_jacobi_pairs)
     int tensor_cores = 1;   // complex64 theta' on the tensor cores (ptebd_set_tensor_cores)
     int polish = 2;         // complex64 Jacobi polish sweep: 0 none, 1 gated SVDs, 2 gated and tSU
     cudaStream_t body_stream = nullptr;  // captures the bodies of the FP64 pass's IF nodes (owned)
@@ -320,6 +321,7 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     a.stabilise = gated ? 1 : 0;
     a.max_sweeps = 40;
     a.nw = st->jacobi_nw;
+    a.pairs = st->jacobi_pairs;
     a.tensor_cores = st->tensor_cores;
     a.polish = (gated && st->polish >= 1) || (!gated && st->polish >= 2) ? 1 : 0;
     a.wait_test = st->wait_test;
@@ -864,7 +866,7 @@ struct TuneKey {
         return std::tie(chip, precision, n_sites, g) < std::tie(o.chip, o.precision, o.n_sites, o.g);
     }
 };
-struct TuneChoice { int nw, chunks; };
+struct TuneChoice { int nw, chunks, pairs; };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tuned;
 
@@ -936,6 +938,7 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
         auto it = g_tuned.find(tune_key(st));
         if (it != g_tuned.end()) {
             st->jacobi_nw = it->second.nw;
+            st->jacobi_pairs = it->second.pairs;
             st->chunk_streams = it->second.chunks;
         }
     }
@@ -967,6 +970,13 @@ int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw) {
     return PTEBD_OK;
 }
 
+int ptebd_set_jacobi_pairs(ptebd_state* st, int32_t pairs) {
+    if (!st) return PTEBD_ERR_INVALID;
+    if (pairs != 1 && pairs != 2) return set_err(st, PTEBD_ERR_INVALID, "Jacobi columns per warp must be 1 or 2");
+    st->jacobi_pairs = pairs;
+    return PTEBD_OK;
+}
+
 int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t gates_on_device, void* scratch,
                    size_t scratch_bytes, double* best) {
     if (!st) return PTEBD_ERR_INVALID;
@@ -979,15 +989,15 @@ int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t
     if (nb > 0 && !gates) return set_err(st, PTEBD_ERR_INVALID, "null gates");
     int rc = sync_and_check(st);
     if (rc) return rc;
-    // candidates: block widths x chunk counts the workspace can run concurrently
-    std::vector<int> widths = {0};
-    if (st->cfg.precision == PTEBD_MIXED) widths = {16, 8};
+    // candidates: (block width, columns per warp) x chunk counts the workspace can run concurrently
+    std::vector<std::pair<int, int>> widths = {{0, 1}};
+    if (st->cfg.precision == PTEBD_MIXED) widths = {{16, 1}, {16, 2}, {8, 1}};
     std::vector<int> chunks;
     for (int k : {1, 2, 4, 8, 12, 16}) {
         const ChunkPlan p = chunk_plan(st->L, k);
         if (p.k == k && (k == 1 || st->slots >= p.k * p.cap)) chunks.push_back(k);
     }
-    const int saved_nw = st->jacobi_nw, saved_chunks = st->chunk_streams;
+    const int saved_nw = st->jacobi_nw, saved_chunks = st->chunk_streams, saved_pairs = st->jacobi_pairs;
     const bool saved_timing = st->timing;
     st->timing = false;
     CUDA_TRY(st, cudaMemcpyAsync(scratch, st->mem, st->L.state_bytes, cudaMemcpyDeviceToDevice, st->stream));
@@ -998,12 +1008,15 @@ int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t
         return set_err(st, PTEBD_ERR_CUDA, "event creation failed");
     }
     double best_ms = 1e300, default_ms = -1.0;
-    int best_nw = saved_nw, best_chunks = saved_chunks;
+    int best_nw = saved_nw, best_chunks = saved_chunks, best_pairs = saved_pairs;
     const int def_nw = jacobi_block_width(st->cfg.precision, saved_nw);
+    const int def_pairs = def_nw == 16 ? saved_pairs : 1;
     const int def_k = chunk_plan(st->L, saved_chunks).k;
-    for (int nw : widths) {
+    for (const auto& wp : widths) {
+        const int nw = wp.first, pairs = wp.second;
         for (int k : chunks) {
             st->jacobi_nw = nw;
+            st->jacobi_pairs = pairs;
             st->chunk_streams = k;
             if ((rc = ensure_chunk_streams(st, chunk_plan(st->L, k).k))) break;
             float ms = 0.f;
@@ -1025,8 +1038,8 @@ int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t
                 if (!rc) rc = check_device_errors(st);
             }
             if (rc) break;
-            if (jacobi_block_width(st->cfg.precision, nw) == def_nw && k == def_k) default_ms = ms;
-            if (ms < best_ms) { best_ms = ms; best_nw = nw; best_chunks = k; }
+            if (jacobi_block_width(st->cfg.precision, nw) == def_nw && pairs == def_pairs && k == def_k) default_ms = ms;
+            if (ms < best_ms) { best_ms = ms; best_nw = nw; best_chunks = k; best_pairs = pairs; }
         }
         if (rc) break;
     }
@@ -1038,22 +1051,25 @@ int ptebd_autotune(ptebd_state* st, const double* gates, int32_t parity, int32_t
     st->timing = saved_timing;
     if (rc) {
         st->jacobi_nw = saved_nw;
+        st->jacobi_pairs = saved_pairs;
         st->chunk_streams = saved_chunks;
         ensure_chunk_streams(st, chunk_plan(st->L, saved_chunks).k);
         return rc;
     }
     if (er != cudaSuccess || es != cudaSuccess) return set_err(st, PTEBD_ERR_CUDA, "state restore failed");
     st->jacobi_nw = best_nw;
+    st->jacobi_pairs = best_pairs;
     st->chunk_streams = best_chunks;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[tune_key(st)] = TuneChoice{best_nw, best_chunks};
+        g_tuned[tune_key(st)] = TuneChoice{best_nw, best_chunks, best_pairs};
     }
     if (best) {
         best[0] = jacobi_block_width(st->cfg.precision, best_nw);
         best[1] = best_chunks ? best_chunks : chunk_plan(st->L, 0).k;
         best[2] = best_ms;
         best[3] = default_ms;
+        best[4] = best_pairs;
     }
     return ensure_chunk_streams(st, chunk_plan(st->L, best_chunks).k);
 }

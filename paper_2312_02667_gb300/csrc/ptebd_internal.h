@@ -102,6 +102,7 @@ struct LayerArgs {
     int wait_test;    // test of the bounded waits: one hand-off wait per CTA targets a count nothing
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
     int nw;           // Jacobi block width requested (0: the default; 8 or 16 for complex64)
+    int pairs;        // complex64, width 16: I columns per warp (1: 16 warps; 2: 8 warps, two pairs a round)
     int tensor_cores; // complex64 theta' and the Gamma GEMM of gated bonds on the tensor cores
                       // (tcgen05, 3xTF32) when chip >= 64
     int polish;       // complex64 Jacobi: one last sweep at the tighter threshold (see Eps::polish)

@@ -383,6 +383,57 @@ __device__ __forceinline__ bool pair_rotate(cx_t<R> (&a)[RPL], cx_t<R> (&b)[RPL]
     return true;
 }
 
+// Two independent column pairs (a0, b0) and (a1, b1) of one warp, complex64 in
+// the pair-split layout: the test and rotation of pair_rotate for each, with the
+// two instruction streams interleaved (dot products, shuffle reductions,
+// rotation parameters, rotations), so that the latency of one pair's chain is
+// covered by the other's work.  v0 / v1: the pair exists.  The rotated b0 / b1
+// go to the shared-memory slots bs0 / bs1; r0 / r1 report which pairs rotated.
+template <int RPL>
+__device__ __forceinline__ void pair_rotate2(float2 (&a0)[RPL], float2 (&b0)[RPL], float& al0, float& be0, bool v0,
+                                             float2 (&a1)[RPL], float2 (&b1)[RPL], float& al1, float& be1, bool v1,
+                                             float tol2, float big2, bool& big, float2* bs0, float2* bs1, bool& r0,
+                                             bool& r1) {
+    float gr0, gi0, gr1, gi1;
+    dot_split<RPL>(a0, b0, gr0, gi0);
+    dot_split<RPL>(a1, b1, gr1, gi1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float x0 = __shfl_xor_sync(0xffffffffu, gr0, o), y0 = __shfl_xor_sync(0xffffffffu, gi0, o);
+        const float x1 = __shfl_xor_sync(0xffffffffu, gr1, o), y1 = __shfl_xor_sync(0xffffffffu, gi1, o);
+        gr0 += x0; gi0 += y0; gr1 += x1; gi1 += y1;
+    }
+    const float g20 = gr0 * gr0 + gi0 * gi0, g21 = gr1 * gr1 + gi1 * gi1;
+    r0 = v0 && (g20 > (tol2 * al0) * be0);
+    r1 = v1 && (g21 > (tol2 * al1) * be1);
+    if (!(r0 || r1)) return;
+    big = big || (r0 && g20 > (big2 * al0) * be0) || (r1 && g21 > (big2 * al1) * be1);
+    // a pair that does not rotate gets harmless parameters (never applied)
+    const RotParams<float> p0 = r0 ? rot_params(al0, be0, gr0, gi0, g20) : RotParams<float>{0.f, 0.f, 0.f, 0.f};
+    const RotParams<float> p1 = r1 ? rot_params(al1, be1, gr1, gi1, g21) : RotParams<float>{0.f, 0.f, 0.f, 0.f};
+    if (r0 && r1) {
+        rotate_split<RPL, false, true>(a0, b0, p0, nullptr, bs0);
+        rotate_split<RPL, false, true>(a1, b1, p1, nullptr, bs1);
+    } else if (r0) {
+        rotate_split<RPL, false, true>(a0, b0, p0, nullptr, bs0);
+    } else {
+        rotate_split<RPL, false, true>(a1, b1, p1, nullptr, bs1);
+    }
+    if (r0) {
+        float al2 = al0 - p0.tg, be2 = be0 + p0.tg;
+        if (!(al2 > 0.125f * al0)) al2 = col_norm2<float, RPL>(a0);
+        if (!(be2 > 0.125f * be0)) be2 = col_norm2<float, RPL>(b0);
+        al0 = al2;
+        be0 = be2;
+    }
+    if (r1) {
+        float al2 = al1 - p1.tg, be2 = be1 + p1.tg;
+        if (!(al2 > 0.125f * al1)) al2 = col_norm2<float, RPL>(a1);
+        if (!(be2 > 0.125f * be1)) be2 = col_norm2<float, RPL>(b1);
+        al1 = al2;
+        be1 = be2;
+    }
+}
 
 template <typename C, int RPL>
 __device__ __forceinline__ int lane_row(int lane, int q) {
@@ -458,9 +509,14 @@ __device__ __forceinline__ void slot_store(const C (&v)[RPL], C* col, int lane) 
 constexpr int kSortN = 512;
 constexpr int kShInts = 8;  // shared ints ahead of the slot round counters
 
-template <typename R, int NW, int RPL>
+// CPW: columns of the register block per warp.  1: NW warps, one I column
+// each; 2 (complex64, RPL >= 2 only): NW / 2 warps, each holding I columns
+// 2w and 2w + 1 and meeting two J columns per round (pair_rotate2).
+template <typename R, int NW, int RPL, int CPW = 1>
 __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int cols, int j, unsigned char* smem) {
     using C = cx_t<R>;
+    static_assert(CPW == 1 || (CPW == 2 && std::is_same<R, float>::value && RPL >= 2), "two columns per warp: complex64, pair-split layout");
+    constexpr int NWARPS = NW / CPW;
     const int ldw = A.ldw;
     const int mpad = ldw;  // rows per column slot in shared memory
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -533,7 +589,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     // rewritten in the pair-split layout on the way.
     auto norm_pass = [&](bool want_max, bool to_split) {
         R mx = 0;
-        for (int c = warp; c < cols; c += NW) {
+        for (int c = warp; c < cols; c += NWARPS) {
             R s0 = 0, s1 = 0;
             if constexpr (PairRows<C, RPL>::on) {
                 float4* col = reinterpret_cast<float4*>(W + (size_t)c * ldw);
@@ -579,7 +635,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             if (sh[2] > 0 && (ex >= Eps<R>::range_e || ex < -Eps<R>::range_e)) {
                 scale_e = ex;
                 const R f = ldexp((R)1, -scale_e);
-                for (int c = warp; c < cols; c += NW)
+                for (int c = warp; c < cols; c += NWARPS)
                     for (int r = lane; r < rows; r += 32) {
                         C v = W[(size_t)c * ldw + r];
                         v.x *= f; v.y *= f;
@@ -622,13 +678,21 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
             // all earlier bulk stores must have landed before plain loads of block I
             if (tid == 0) { bulk_wait_all(); fence_async_global(); }
             __syncthreads();
-            const bool mine = I * NW + warp < cols;
-            const int my_col = mine ? cperm[I * NW + warp] : 0;  // physical column
-            C a[RPL];
-            col_load<C, RPL>(a, W + (size_t)my_col * ldw, lane, rows, mine);
-            // ---- intra-block pairs of I (round-robin), in shared memory
-            slot_store<C, RPL>(a, bufI + (size_t)warp * mpad, lane);
-            if (lane == 0) in2[warp] = mine ? (R)nrm2[my_col] : (R)0;
+            // this warp's columns CPW warp + k of block I
+            bool mine[CPW];
+            int my_col[CPW];  // physical columns
+            C a[CPW][RPL];
+            R al[CPW];
+#pragma unroll
+            for (int k = 0; k < CPW; ++k) {
+                const int ic = CPW * warp + k;
+                mine[k] = I * NW + ic < cols;
+                my_col[k] = mine[k] ? cperm[I * NW + ic] : 0;
+                col_load<C, RPL>(a[k], W + (size_t)my_col[k] * ldw, lane, rows, mine[k]);
+                // ---- intra-block pairs of I (round-robin), in shared memory
+                slot_store<C, RPL>(a[k], bufI + (size_t)ic * mpad, lane);
+                if (lane == 0) in2[ic] = mine[k] ? (R)nrm2[my_col[k]] : (R)0;
+            }
             __syncthreads();
             for (int r = 0; r < NW - 1; ++r) {
                 if (warp < NW / 2) {
@@ -652,8 +716,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                 }
                 __syncthreads();
             }
-            slot_load<C, RPL>(a, bufI + (size_t)warp * mpad, lane);
-            R al = in2[warp];
+#pragma unroll
+            for (int k = 0; k < CPW; ++k) {
+                slot_load<C, RPL>(a[k], bufI + (size_t)(CPW * warp + k) * mpad, lane);
+                al[k] = in2[CPW * warp + k];
+            }
 
             // ---- cross pairs with every later block J, streamed by TMA
             if (I + 1 < nb) {
@@ -679,6 +746,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                     const int base = jblocks[cur] * NW;
                     const bool test_wait = A.wait_test && warp == 0 && sweep == 0 && I == 0 && J == 1;
                     for (int r = 0; r < NW && ok; ++r) {
+                      if constexpr (CPW == 1) {
                         const int jc = (warp + r) & (NW - 1);
                         const int lcol = J * NW + jc;
                         if (r > 0) {
@@ -689,11 +757,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         if (!ok) break;
                         if (lcol < cols) {
                             R be = sn2[jc];
-                            if (mine) {
+                            if (mine[0]) {
                                 C y[RPL];
                                 slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                 // the rotated J column goes back to its slot inside the rotation
-                                if (pair_rotate<R, RPL, false, true>(a, y, al, be, tol2, big2, big_w, nullptr,
+                                if (pair_rotate<R, RPL, false, true>(a[0], y, al[0], be, tol2, big2, big_w, nullptr,
                                                                      buf + (size_t)jc * mpad)) {
                                     sn2[jc] = be;  // every lane: the same value
                                     ++rot_w;
@@ -703,6 +771,38 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         }
                         __syncwarp();
                         if (lane == 0) counter_release_add(&done[jc]);
+                      } else {
+                        // I column 2w meets jc0, which this warp's column 2w + 1 met in
+                        // round r - 1 (no wait); I column 2w + 1 meets jc1, which
+                        // column 2w + 2 (warp w + 1) met in round r - 1
+                        const int jc0 = (2 * warp + r) & (NW - 1), jc1 = (2 * warp + 1 + r) & (NW - 1);
+                        const int lc0 = J * NW + jc0, lc1 = J * NW + jc1;
+                        if (r > 0) {
+                            const bool t = test_wait && r == 1;
+                            ok = counter_wait_bounded(&done[jc1], t ? 0x7fffffff : base + r, &sh[1],
+                                                      t ? (1ll << 20) : (1ll << 31));
+                        }
+                        if (!ok) break;
+                        R be0 = lc0 < cols ? sn2[jc0] : (R)0, be1 = lc1 < cols ? sn2[jc1] : (R)0;
+                        C y0[RPL], y1[RPL];
+                        slot_load<C, RPL>(y0, buf + (size_t)jc0 * mpad, lane);
+                        slot_load<C, RPL>(y1, buf + (size_t)jc1 * mpad, lane);
+                        bool r0, r1;
+                        pair_rotate2<RPL>(a[0], y0, al[0], be0, mine[0] && lc0 < cols, a[CPW - 1], y1, al[CPW - 1], be1,
+                                          mine[CPW - 1] && lc1 < cols, tol2, big2, big_w, buf + (size_t)jc0 * mpad,
+                                          buf + (size_t)jc1 * mpad, r0, r1);
+                        if (r0) { sn2[jc0] = be0; ++rot_w; }
+                        if (r1) { sn2[jc1] = be1; ++rot_w; }
+                        if (r == NW - 1) {
+                            if (lc0 < cols) nrm2[cperm[lc0]] = (double)be0;
+                            if (lc1 < cols) nrm2[cperm[lc1]] = (double)be1;
+                        }
+                        __syncwarp();
+                        if (lane == 0) {
+                            counter_release_add(&done[jc0]);
+                            counter_release_add(&done[jc1]);
+                        }
+                      }
                     }
                     if (!ok) atomicOr(&sh[1], 1);
                     phase[cur] ^= 1u;
@@ -725,10 +825,12 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                 }
             }
             // write block I back
-            if (mine) {
-                col_store<C, RPL>(a, W + (size_t)my_col * ldw, lane, rows);
-                if (lane == 0) nrm2[my_col] = (double)al;
-            }
+#pragma unroll
+            for (int k = 0; k < CPW; ++k)
+                if (mine[k]) {
+                    col_store<C, RPL>(a[k], W + (size_t)my_col[k] * ldw, lane, rows);
+                    if (lane == 0) nrm2[my_col[k]] = (double)al[k];
+                }
             fence_async_global();
             __syncthreads();
         }
@@ -780,7 +882,7 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     // the pair-split layout turned back into plain complex columns
     double* nrm = A.norms + (size_t)j * ldw;
     const R unscale = ldexp((R)1, scale_e);
-    for (int c = warp; c < cols; c += NW) {
+    for (int c = warp; c < cols; c += NWARPS) {
         double acc = 0.0;
         if constexpr (PairRows<C, RPL>::on) {
             float4* col = reinterpret_cast<float4*>(W + (size_t)c * ldw);
@@ -854,6 +956,41 @@ __global__ void __launch_bounds__(NW * 32, JacobiMinBlocks<R, NW>::v) k_jacobi(L
 // Block width (columns of the register block = warps of the CTA).  complex64:
 // 16 by default, 8 selectable (a.nw); complex128: 8 (16 columns of complex128
 // stages would not fit in shared memory).
+// Two columns per warp (jacobi_body with CPW = 2): NW / 2 warps.  Matrices of at
+// most 32 rows (one entry per lane, no pair-split layout) take jacobi_body with
+// NW / 2 columns, one per warp, instead; the prologue sets up the shared-memory
+// layout of the body it calls.
+template <int NW>
+__global__ void __launch_bounds__(NW * 16, 1) k_jacobi2(LayerArgs<float> A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int j = blockIdx.x;
+    const int32_t* d = A.dims + j * kDims;
+    if (A.refine == 1 && d[D_REFINE] != 1) return;
+    const int rows = A.pass == 1 ? 2 * d[D_CL] : d[D_ROWS];
+    const int cols = A.pass == 1 ? d[D_CM] : d[D_COLS];
+    float2* W = A.w + (size_t)j * A.ldw * A.ldw;
+    const int qa = (rows + 31) / 32;
+    const int nwl = qa <= 1 ? NW / 2 : NW;  // columns per block of the body called
+    const size_t stage_elems = (size_t)3 * nwl * A.ldw;
+    float2* z = reinterpret_cast<float2*>(smem);
+    for (size_t e = threadIdx.x; e < stage_elems; e += blockDim.x) z[e] = make_float2(0.f, 0.f);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(z + stage_elems);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+        int* sh = reinterpret_cast<int*>(reinterpret_cast<float*>(bar + 2) + 3 * nwl);
+        for (int i = 0; i < kShInts + 2 * nwl; ++i) sh[i] = 0;
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (qa <= 1) jacobi_body<float, NW / 2, 1, 1>(A, W, rows, cols, j, smem);
+    else if (qa <= 2) jacobi_body<float, NW, 2, 2>(A, W, rows, cols, j, smem);
+    else if (qa <= 4) jacobi_body<float, NW, 4, 2>(A, W, rows, cols, j, smem);
+    else if (qa <= 8) jacobi_body<float, NW, 8, 2>(A, W, rows, cols, j, smem);
+    else jacobi_body<float, NW, 16, 2>(A, W, rows, cols, j, smem);
+}
+
 template <typename R> struct JacobiNW;
 template <> struct JacobiNW<float> { static constexpr int v = 16; };
 template <> struct JacobiNW<double> { static constexpr int v = 8; };
@@ -877,10 +1014,14 @@ template <typename R> cudaError_t jacobi_prepare() {
     constexpr int NW = JacobiNW<R>::v;
     cudaError_t e = cudaFuncSetAttribute(k_jacobi<R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, NW));
-    if constexpr (std::is_same<R, float>::value)
+    if constexpr (std::is_same<R, float>::value) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_jacobi<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, 8));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_jacobi2<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)jacobi_smem_bytes(prec, 2 * PTEBD_CHI_LIMIT, 16));
+    }
     return e;
 }
 
@@ -891,7 +1032,9 @@ template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStrea
     if constexpr (std::is_same<R, double>::value) {
         k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);  // complex128: 8-column blocks only
     } else {
-        if (nw == 8)
+        if (nw == 16 && a.pairs == 2)  // two columns per warp: 8 warps
+            k_jacobi2<16><<<a.count, 16 * 16, smem, s>>>(a);
+        else if (nw == 8)
             k_jacobi<R, 8><<<a.count, 8 * 32, smem, s>>>(a);
         else
             k_jacobi<R, 16><<<a.count, 16 * 32, smem, s>>>(a);

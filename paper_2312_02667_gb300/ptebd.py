@@ -39,7 +39,7 @@ EXPORTS = (
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
     "ptebd_set_chunk_streams", "ptebd_test_wait_timeout", "ptebd_alu_peak", "ptebd_set_regauge_precision",
-    "ptebd_set_jacobi_width", "ptebd_autotune", "ptebd_set_tensor_cores",
+    "ptebd_set_jacobi_width", "ptebd_set_jacobi_pairs", "ptebd_autotune", "ptebd_set_tensor_cores",
     "ptebd_set_svd_polish",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor", "resolve")
@@ -107,6 +107,7 @@ _SIGS = {
     "ptebd_alu_peak": (ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _P, _D, _D),
     "ptebd_set_regauge_precision": (_P, ctypes.c_int32),
     "ptebd_set_jacobi_width": (_P, ctypes.c_int32),
+    "ptebd_set_jacobi_pairs": (_P, ctypes.c_int32),
     "ptebd_set_tensor_cores": (_P, ctypes.c_int32),
     "ptebd_set_svd_polish": (_P, ctypes.c_int32),
     "ptebd_autotune": (_P, _D, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _D),
@@ -344,12 +345,16 @@ def ptebd_set_jacobi_width(h, nw):
     _check(lib.ptebd_set_jacobi_width(h, int(nw)), h)
 
 
+def ptebd_set_jacobi_pairs(h, pairs):
+    _check(lib.ptebd_set_jacobi_pairs(h, int(pairs)), h)
+
+
 def ptebd_autotune(h, gates, parity, scratch_ptr, scratch_bytes):
-    """(block width, chunks, best ms, ms of the previous configuration)."""
+    """(block width, chunks, best ms, ms of the previous configuration, columns per warp)."""
     ptr, on_dev, keep = _gates_arg(gates)
-    best = np.zeros(4)
+    best = np.zeros(5)
     _check(lib.ptebd_autotune(h, ptr, int(parity), on_dev, _P(scratch_ptr), int(scratch_bytes), _dptr(best)), h)
-    return int(best[0]), int(best[1]), float(best[2]), float(best[3])
+    return int(best[0]), int(best[1]), float(best[2]), float(best[3]), int(best[4])
 
 
 def ptebd_test_wait_timeout(h, enable):
@@ -613,6 +618,9 @@ class State:
 
     def set_jacobi_width(self, nw):
         ptebd_set_jacobi_width(self.handle, nw)
+
+    def set_jacobi_pairs(self, pairs):
+        ptebd_set_jacobi_pairs(self.handle, pairs)
 
     def set_tensor_cores(self, enable):
         ptebd_set_tensor_cores(self.handle, enable)

@@ -37,12 +37,13 @@ def test_autotune_leaves_the_state_unchanged(ptebd, prec):
     gam0, lam0 = snapshot(st)
     w0 = st.work_counters()
     _, layers0 = st.svd_sweeps()
-    nw, chunks, best_ms, prev_ms = st.autotune(circuit[depth][2], circuit[depth][0])
+    nw, chunks, best_ms, prev_ms, pairs = st.autotune(circuit[depth][2], circuit[depth][0])
     gam1, lam1 = snapshot(st)
     assert all(np.array_equal(a, b) for a, b in zip(gam0, gam1))
     assert all(np.array_equal(a, b) for a, b in zip(lam0, lam1))
     assert st.work_counters() == w0 and st.svd_sweeps()[1] == layers0
     assert nw in ((8, 16) if prec == "mixed" else (8,)) and chunks >= 1 and 0 < best_ms
+    assert pairs == 1 or (prec == "mixed" and nw == 16 and pairs == 2)
     assert prev_ms < 0 or best_ms <= prev_ms
     # the tuned handle then runs that layer as the oracle does
     ref = to_oracle(st)
@@ -53,16 +54,17 @@ def test_autotune_leaves_the_state_unchanged(ptebd, prec):
     for b in range(n - 1):
         compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-10 if prec == "fp64" else 1e-5, 1e-12, chi)
     assert fidelity(got, ref) >= 1 - (1e-9 if prec == "fp64" else 1e-6)
-    print(f"{prec}: tuned width {nw}, chunks {chunks}: {best_ms:.2f} ms (before: {prev_ms:.2f} ms)")
+    print(f"{prec}: tuned width {nw} x {pairs}, chunks {chunks}: {best_ms:.2f} ms (before: {prev_ms:.2f} ms)")
 
 
-@pytest.mark.parametrize("nw", [8, 16])
-def test_jacobi_width_matches_oracle_and_repeats_bitwise(ptebd, nw):
+@pytest.mark.parametrize("nw,pairs", [(8, 1), (16, 1), (16, 2)])
+def test_jacobi_width_matches_oracle_and_repeats_bitwise(ptebd, nw, pairs):
     n, chi, depth = 32, 64, 8
     circuit = inputs.brickwork_circuit(43, n, depth)
     ref = oracle.product_state(n)
     st = ptebd.State(n, chi, "mixed", cutoff=1e-12)
     st.set_jacobi_width(nw)
+    st.set_jacobi_pairs(pairs)
     for parity, bonds, gates in circuit:
         load_into(st, ref)
         st.apply_layer(gates, parity)
@@ -79,3 +81,34 @@ def test_jacobi_width_matches_oracle_and_repeats_bitwise(ptebd, nw):
         runs.append(snapshot(st))
     assert all(np.array_equal(a, b) for a, b in zip(runs[0][0], runs[1][0]))
     assert all(np.array_equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))
+
+
+@pytest.mark.parametrize("chi,g", [(256, 1), (32, 0)])
+def test_two_columns_per_warp_bit_identical(ptebd, chi, g):
+    """Two I columns per warp visit the same column pairs in the same order as
+    one per warp: the states agree bit for bit (theta' 512 x 512 at chi 256,
+    tSU factors included; 64 x 64 at chi 32)."""
+    n, depth = 24, 10
+    circuit = inputs.brickwork_circuit(47, n, depth)
+    runs = []
+    for pairs in (1, 2):
+        st = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=g)
+        st.set_jacobi_width(16)
+        st.set_jacobi_pairs(pairs)
+        for parity, bonds, gates in circuit:
+            st.apply_layer(gates, parity)
+        runs.append((snapshot(st), st.work_counters()))
+        st.close()
+    (g1, l1), w1 = runs[0]
+    (g2, l2), w2 = runs[1]
+    assert max(len(l) for l in l1) == chi
+    assert all(np.array_equal(a, b) for a, b in zip(g1, g2))
+    assert all(np.array_equal(a, b) for a, b in zip(l1, l2))
+    assert w1[:8] == w2[:8]  # same visits, rotations, sweeps
+
+
+def test_jacobi_pairs_rejects_other_values(ptebd):
+    st = ptebd.State(8, 8, "mixed")
+    with pytest.raises(ptebd.PtebdError):
+        st.set_jacobi_pairs(3)
+    st.close()

@@ -88,6 +88,8 @@ def parse():
     p.add_argument("--routed", action="store_true",
                    help="the 2D routed workload (32x32 lattice, depth 8, chi 128, compiled sparse layers) alone")
     p.add_argument("--no-tune", action="store_true", help="--serving: skip the autotuned pass")
+    p.add_argument("--serving-circuits", type=int, default=64,
+                   help="--serving: the first K of the 64 seeded circuits (for the slow FP64 pass)")
     p.add_argument("--serial", action="store_true",
                    help="--serving: advance the states one by one (no batch graph), for comparison")
     p.add_argument("--no-tensor-cores", action="store_true",
@@ -610,6 +612,9 @@ def serving_bench(args):
     ns = rng.integers(50, 501, k)
     ds = rng.integers(8, 25, k)
     chis = rng.choice([32, 64, 128, 256], k)
+    # --serving-circuits K: the first K circuits of the same seeded set
+    k = max(1, min(k, args.serving_circuits))
+    ns, ds, chis = ns[:k], ds[:k], chis[:k]
     states = [ptebd.State(int(ns[i]), int(chis[i]), args.precision, resolve=args.resolve) for i in range(k)]
     if args.no_tensor_cores:
         for st in states:
@@ -660,7 +665,7 @@ def serving_bench(args):
                 "unit": "bond-SVDs/s", "value": gated / wall_u, "higher_is_better": True,
                 "untuned": {"value": gated / wall_u, "wall_s": wall_u, "device_s": dev_u, "first_pass_s": first_u},
                 "gated_bond_updates": gated, "fp64_resolved_bonds": resolved, "precision": args.precision,
-                "tensor_cores": not args.no_tensor_cores}
+                "tensor_cores": not args.no_tensor_cores, "circuits": k}
     # tune one representative per key at the middle of its circuit
     def key(i):
         return (int(chis[i]), int(ns[i] - 1).bit_length())
@@ -696,7 +701,7 @@ def serving_bench(args):
             "circuit_layers_per_s": float(ds.sum()) / wall_t, "batch_layers_per_s": len(layers) / wall_t,
             "gated_bond_updates": gated, "fp64_resolved_bonds": resolved,
             "circuits": k, "circuit_layers": int(ds.sum()), "batch_layers": len(layers),
-            "config": {"workload": "64 circuits, N ~ U[50, 500], depth ~ U[8, 24], chi_max in {32, 64, 128, 256}, "
+            "config": {"workload": f"{k} of 64 seeded circuits, N ~ U[50, 500], depth ~ U[8, 24], chi_max in {{32, 64, 128, 256}}, "
                                    f"Haar U(4) brickwork, cutoff 1e-12, {args.precision}, g = 0, from |0...0>",
                        "seed": 64}}
 

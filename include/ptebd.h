@@ -216,9 +216,14 @@ int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw);
  * (no counterpart in the paper: a scheduling choice).  pairs = 1 (the
  * default): 16 warps, one I column each, one column pair a round; pairs = 2:
  * 8 warps, each holding two I columns and rotating two independent column
- * pairs a round with their instruction streams interleaved.  The same pairs
- * meet in the same order (bit-identical results to pairs = 1); width 8 and
- * complex128 ignore it.  PTEBD_ERR_INVALID for other values. */
+ * pairs a round with their instruction streams interleaved.  Matrices of
+ * more than 32 rows see their column pairs in the same order as with
+ * pairs = 1; smaller ones run with 8-column blocks, so results differ from
+ * pairs = 1 by rounding (both bit-identical run to run).  Measured at N = 1024,
+ * chi = 256: the SVD takes 19% longer than with pairs = 1 (half the warps,
+ * issue activity 38% against 51%), so it is an autotuner candidate, not the
+ * default.  Width 8 and complex128 ignore it.  PTEBD_ERR_INVALID for other
+ * values. */
 int ptebd_set_jacobi_pairs(ptebd_state* st, int32_t pairs);
 
 /* Autotuner (no counterpart in the paper: a scheduling choice of the library).

@@ -315,11 +315,11 @@ def run_ours(args, rank, world, local_rank):
         peak_note = "measured in this run: FP64 FMA probe (ptebd_alu_peak)"
     # launches in the timed region: per chunk, a gated stage runs 6 kernels (Gamma
     # is two) and a tSU half-step 9; the FP64 resolution pass of a mixed state adds
-    # 5 and 8 (their CTAs return at once unless a bond was left undecided); one more
+    # 6 and 8 (their CTAs return at once unless a bond was left undecided); one more
     # adds the chunks' eps sums
     n_chunks = args.chunk_streams or min(8, max(1, (n // 2) // 32))
     resolve = args.precision == "mixed"
-    per_layer = n_chunks * ((11 if resolve else 6) + 2 * (17 if resolve else 9) * args.g) + (1 if n_chunks > 1 else 0)
+    per_layer = n_chunks * ((12 if resolve else 6) + 2 * (17 if resolve else 9) * args.g) + (1 if n_chunks > 1 else 0)
     gpu_launches = args.steps * per_layer
 
     # ---- e2e: host gates (pinned) in, truncation metric out, through the C ABI

@@ -371,6 +371,7 @@ LayerArgs<double> refine_args(ptebd_state* st, const LayerArgs<float>& c, int ba
     a.mode = c.mode; a.pass = 0;
     a.bond_eps = c.bond_eps; a.bond_nu = c.bond_nu; a.bond_rank = c.bond_rank; a.bond_sweeps = c.bond_sweeps;
     a.totals = c.totals; a.err = c.err; a.work = c.work;
+    a.w32 = c.w;  // a gated bond's FP64 SVD starts from the complex64 one (k_precond)
     return a;
 }
 
@@ -384,6 +385,8 @@ int launch_pass(ptebd_state* st, LayerArgs<R> a, bool gated, cudaStream_t s, W&&
               kf = a.refine ? PTEBD_K_RESOLVE : PTEBD_K_FACTOR;
     if (gated) {
         CUDA_TRY(st, wrap(kt, [&] { return launch_theta<R, G>(a, s); }));
+        if constexpr (std::is_same<R, double>::value)
+            if (a.refine == 1 && a.w32) CUDA_TRY(st, wrap(kt, [&] { return launch_precond(a, s); }));
         CUDA_TRY(st, wrap(ks, [&] { return launch_jacobi<R>(a, s); }));
         CUDA_TRY(st, wrap(kc, [&] { return launch_truncate<R>(a, s); }));
         CUDA_TRY(st, wrap(kg, [&] { return launch_gamma<R, G>(a, s); }));

@@ -98,6 +98,9 @@ struct LayerArgs {
                               // resolution pass; the complex64 truncation sets it when it leaves a bond undecided
     int refine;       // 1: this launch is the FP64 resolution pass (only bonds with D_REFINE = 1 run);
                       // 2: an FP64 pass over every bond of a complex64 state (FP64 regauge)
+    const float2* w32;  // the FP64 resolution of a gated bond: the complex64 pass's rotated columns
+                        // U32 S32 of the same slots (with their FP64 norms still in `norms`); the
+                        // FP64 SVD then runs on B = M^dag U32 (launch_precond) instead of on M
     int eps_mode, stabilise, max_sweeps;
     int wait_test;    // test of the bounded waits: one hand-off wait per CTA targets a count nothing
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
@@ -134,6 +137,8 @@ template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStr
 template <typename R, typename G = cx_t<R>> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R, typename G = cx_t<R>> cudaError_t launch_xform(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s);
+// the FP64 resolution of gated bonds: B = M^dag U32 into w (k_precond)
+cudaError_t launch_precond(const LayerArgs<double>& a, cudaStream_t s);
 // pass 1 of the tSU SVD: an orthonormal basis of the columns of X (ptebd_orth.cu)
 template <typename R> cudaError_t launch_orth(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R> cudaError_t orth_prepare();   // raises its dynamic smem limit

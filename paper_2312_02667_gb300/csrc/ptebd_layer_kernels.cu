@@ -73,6 +73,20 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
     const int cl = a.chi[b], cm = a.chi[b + 1], cr = a.chi[b + 2];
     // tSU (mode 1) always stores theta^dag: its SVD goes through the factors
     const bool tall = a.mode == 0 && cl >= cr;
+    // The FP64 resolution of a gated bond runs its SVD on B = M^dag U32 (k_precond),
+    // whose rotated columns are M's right singular vectors: the Gamma kernels then
+    // take the bond in the other orientation, so w0 gets M^dag (the layout the other
+    // orientation stores) and the dims are switched to it: rows = cols = n, the
+    // columns of M.  w is left to k_precond.
+    const bool precond = a.refine == 1 && a.mode == 0 && a.w32 != nullptr;
+    const bool wtall = precond ? !tall : tall;
+    if (precond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        int32_t* d = a.dims + j * kDims;
+        const int n = tall ? 2 * cr : 2 * cl;
+        d[D_TALL] = tall ? 0 : 1;
+        d[D_ROWS] = n;
+        d[D_COLS] = n;
+    }
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && a.refine != 1) {
         int32_t* d = a.dims + j * kDims;
         d[D_CL] = cl; d[D_CM] = cm; d[D_CR] = cr; d[D_TALL] = tall ? 1 : 0; d[D_BOND] = b;
@@ -190,11 +204,12 @@ __global__ void __launch_bounds__(256) k_theta(LayerArgs<R> a) {
                         v = acc[sp][tp][i][q];
                     }
                     const size_t r = (size_t)sp * cl + alpha, c = (size_t)tp * cr + gamma;
-                    if (tall) {
-                        W[c * ldw + r] = v; W0[c * ldw + r] = v;
+                    if (wtall) {
+                        if (!precond) W[c * ldw + r] = v;
+                        W0[c * ldw + r] = v;
                     } else {
                         const C vc = cconj(v);
-                        if (a.mode == 0) W[r * ldw + c] = vc;
+                        if (a.mode == 0 && !precond) W[r * ldw + c] = vc;
                         W0[r * ldw + c] = vc;
                     }
                 }
@@ -544,6 +559,81 @@ __global__ void __launch_bounds__(256) k_gamma_gemm(LayerArgs<R> a) {
         }
 }
 
+// -------------------------------------------- FP64 resolution, gated bond --
+// B = M^dag U32 for a gated bond left undecided by the complex64 truncation:
+// M (m x n) is the matrix the complex64 Jacobi ran on, held in w0 as M^dag
+// (k_theta's preconditioned store), and U32 = the complex64 pass's rotated
+// columns w32 divided by their norms (a zero column stays zero).  The FP64 SVD
+// then runs on B (n x n, into w): B = V S U^dag U32, and with U32 unitary up to
+// the complex64 Jacobi's orthogonality (a few 1e-6) this is M's right singular
+// vectors times S up to a multiplicative perturbation of that size, which moves
+// every singular value by that relative amount at most, the smallest included,
+// and leaves an exact zero of S exactly zero.  Its columns start nearly
+// orthogonal except inside the complex64 noise, so the FP64 sweeps converge in
+// fewer steps than from M.  The dims were switched by k_theta: D_TALL is the
+// other orientation, D_ROWS = D_COLS = n; m = 2 chi_{b-1} (originally tall) or
+// 2 chi_{b+1}.
+// grid (ceil(2 chip / 32), ceil(2 chip / 32), count), 256 threads, 2x2 outputs a thread.
+__global__ void __launch_bounds__(256) k_precond(LayerArgs<double> a) {
+    const int j = blockIdx.z;
+    const int32_t* d = a.dims + j * kDims;
+    if (d[D_REFINE] != 1) return;
+    const int n = d[D_ROWS];
+    const int m = d[D_TALL] ? 2 * d[D_CR] : 2 * d[D_CL];
+    const int i0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    if (i0 >= n || c0 >= n) return;
+    const size_t ldw = a.ldw;
+    const double2* Mh = a.w0 + (size_t)j * ldw * ldw;  // M^dag: n x m, column-major
+    const float2* U = a.w32 + (size_t)j * ldw * ldw;    // U32 S32: m x n
+    const double* nrm = a.norms + (size_t)j * ldw;
+    double2* B = a.w + (size_t)j * ldw * ldw;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ double2 ps[16][33], qs[16][33];
+    __shared__ double qscl[32];
+    if (threadIdx.x < 32) {
+        const int c = c0 + threadIdx.x;
+        const double s = c < n ? nrm[c] : 0.0;
+        qscl[threadIdx.x] = s > 0.0 ? 1.0 / s : 0.0;
+    }
+    __syncthreads();
+    double2 acc[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc[i][q] = make_double2(0.0, 0.0);
+    for (int r0 = 0; r0 < m; r0 += 16) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int ii = e & 31, kk = e >> 5;  // M^dag(i0 + ii, r0 + kk): contiguous in ii
+            const int r = r0 + kk;
+            ps[kk][ii] = (i0 + ii < n && r < m) ? Mh[(size_t)r * ldw + i0 + ii] : make_double2(0.0, 0.0);
+            const int kq = e & 15, cc = e >> 4;  // U32(r0 + kq, c0 + cc): contiguous in kq
+            const int rq = r0 + kq;
+            double2 u = make_double2(0.0, 0.0);
+            if (c0 + cc < n && rq < m) {
+                const float2 v = U[(size_t)(c0 + cc) * ldw + rq];
+                u = make_double2((double)v.x * qscl[cc], (double)v.y * qscl[cc]);
+            }
+            qs[kq][cc] = u;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            const double2 p0 = ps[kk][tx], p1 = ps[kk][tx + 16];
+            const double2 q0 = qs[kk][ty], q1 = qs[kk][ty + 16];
+            cfma(acc[0][0], p0, q0); cfma(acc[0][1], p0, q1);
+            cfma(acc[1][0], p1, q0); cfma(acc[1][1], p1, q1);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int row = i0 + tx + 16 * i, col = c0 + ty + 16 * q;
+            if (row < n && col < n) B[(size_t)col * ldw + row] = acc[i][q];
+        }
+}
+
 // ------------------------------------------------------- tSU factors ----
 // For tSU the two-site tensor is theta = X Y with X = diag(Lambda_{b-1}) Gamma_b diag(Lambda_b)
 // (2 chi_{b-1} x chi_b, rows (s, alpha)), so rank(theta) <= chi_b.  Its SVD is taken
@@ -701,6 +791,12 @@ template <typename R, typename G> cudaError_t launch_xform(const LayerArgs<R>& a
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
     dim3 grid((2 * a.chip + 31) / 32, (a.chip + 31) / 32, a.count);
     k_proj<R><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_precond(const LayerArgs<double>& a, cudaStream_t s) {
+    const int tiles = (2 * a.chip + 31) / 32;
+    dim3 grid(tiles, tiles, a.count);
+    k_precond<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_reduce_layer(const double* slot_eps, const double* slot_lognu, int count,

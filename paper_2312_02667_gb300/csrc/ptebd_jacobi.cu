@@ -537,6 +537,15 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     int jblocks[2] = {0, 0};  // J blocks processed so far on each stage
     // squared column norms between blocks (FP64), a table in shared memory
     double* nrm2 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(skey + kSortN) + 7) & ~uintptr_t(7));
+    // complex128 only: per column, bit 0 = rotated in the previous sweep, bit 1 =
+    // rotated in this one.  A pair whose two columns have neither bit set met in
+    // the previous sweep as the same two vectors and was found orthogonal then, so
+    // its dot product is skipped (on the FP64 pipe a dot product costs as much as
+    // a third of a rotation; late sweeps are mostly such checks).
+    constexpr bool kSkip = std::is_same<R, double>::value;
+    unsigned char* rflag = reinterpret_cast<unsigned char*>(nrm2 + kSortN);
+    if constexpr (kSkip)
+        for (int c = tid; c < kSortN; c += blockDim.x) rflag[c] = 1;  // sweep 0 checks every pair
 
     const R tol = (R)(Eps<R>::k * sqrt((double)rows) * Eps<R>::u);
     R tol2 = tol * tol;
@@ -626,6 +635,9 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
     int scale_e = 0;
 
     for (sweep = 0; sweep < A.max_sweeps; ++sweep) {
+        if constexpr (kSkip)
+            if (sweep > 0)
+                for (int c = tid; c < kSortN; c += blockDim.x) rflag[c] = (unsigned char)(rflag[c] >> 1);
         if (tid == 0) { sh[0] = 0; sh[7] = 0; bulk_wait_all(); fence_async_global(); }
         __syncthreads();
         norm_pass(sweep == 0, sweep == 0 && PairRows<C, RPL>::on);
@@ -698,7 +710,9 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                 if (warp < NW / 2) {
                     auto player = [&](int pos) { return pos == 0 ? 0 : 1 + ((pos - 1 + r) % (NW - 1)); };
                     const int p = player(warp), q2 = player(NW - 1 - warp);
-                    if (I * NW + p < cols && I * NW + q2 < cols) {
+                    const bool skip = kSkip && I * NW + p < cols && I * NW + q2 < cols &&
+                                      !(rflag[cperm[I * NW + p]] | rflag[cperm[I * NW + q2]]);
+                    if (I * NW + p < cols && I * NW + q2 < cols && !skip) {
                         C x[RPL], y[RPL];
                         slot_load<C, RPL>(x, bufI + (size_t)p * mpad, lane);
                         slot_load<C, RPL>(y, bufI + (size_t)q2 * mpad, lane);
@@ -709,6 +723,10 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                             if (lane == 0) {
                                 in2[p] = nx;
                                 in2[q2] = ny;
+                                if constexpr (kSkip) {
+                                    rflag[cperm[I * NW + p]] |= 2;
+                                    rflag[cperm[I * NW + q2]] |= 2;
+                                }
                             }
                             ++rot_w;
                         }
@@ -757,7 +775,8 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                         if (!ok) break;
                         if (lcol < cols) {
                             R be = sn2[jc];
-                            if (mine[0]) {
+                            const bool skip = kSkip && mine[0] && !(rflag[my_col[0]] | rflag[cperm[lcol]]);
+                            if (mine[0] && !skip) {
                                 C y[RPL];
                                 slot_load<C, RPL>(y, buf + (size_t)jc * mpad, lane);
                                 // the rotated J column goes back to its slot inside the rotation
@@ -765,6 +784,11 @@ __device__ void jacobi_body(const LayerArgs<R>& A, cx_t<R>* W, int rows, int col
                                                                      buf + (size_t)jc * mpad)) {
                                     sn2[jc] = be;  // every lane: the same value
                                     ++rot_w;
+                                    if constexpr (kSkip)
+                                        if (lane == 0) {
+                                            rflag[my_col[0]] |= 2;
+                                            rflag[cperm[lcol]] |= 2;
+                                        }
                                 }
                             }
                             if (r == NW - 1) nrm2[cperm[lcol]] = (double)be;
@@ -1006,7 +1030,7 @@ size_t jacobi_smem_bytes(int precision, int ldw, int nw) {
     const size_t elem = precision == PTEBD_FP64 ? sizeof(double2) : sizeof(float2);
     const size_t real = precision == PTEBD_FP64 ? sizeof(double) : sizeof(float);
     return (size_t)3 * nw * ldw * elem + 2 * sizeof(uint64_t) + 3 * nw * real + (kShInts + 2 * nw) * sizeof(int) +
-           (size_t)kSortN * (sizeof(int) + sizeof(float)) + 8 + (size_t)kSortN * sizeof(double);
+           (size_t)kSortN * (sizeof(int) + sizeof(float)) + 8 + (size_t)kSortN * sizeof(double) + kSortN;
 }
 
 template <typename R> cudaError_t jacobi_prepare() {

@@ -97,6 +97,8 @@ def parse():
                    help="--serving: advance the states one by one (no batch graph), for comparison")
     p.add_argument("--no-tensor-cores", action="store_true",
                    help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
+    p.add_argument("--svd-polish", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                   help="complex64 polish sweep: 0 none, 1 gated, 2 gated and tSU, 3 tSU (-1: the library's choice)")
     p.add_argument("--jacobi-width", type=int, default=0, choices=[0, 8, 16],
                    help="complex64 Jacobi block width (0: the library's choice)")
     p.add_argument("--jacobi-pairs", type=int, default=0, choices=[0, 1, 2],
@@ -241,6 +243,8 @@ def run_ours(args, rank, world, local_rank):
         st.set_chunk_streams(args.chunk_streams)
     if args.jacobi_width:
         st.set_jacobi_width(args.jacobi_width)
+    if args.svd_polish >= 0:
+        st.set_svd_polish(args.svd_polish)
     if args.jacobi_pairs:
         st.set_jacobi_pairs(args.jacobi_pairs)
     n_layers = args.prefill + args.warmup + args.steps
@@ -373,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
         "tsu_bonds_per_step": args.g * (n - 1),
         "chunk_streams": n_chunks,
         "jacobi_width": args.jacobi_width or "library choice",
+        "svd_polish": args.svd_polish if args.svd_polish >= 0 else "library choice",
         "jacobi_columns_per_warp": args.jacobi_pairs or "library choice",
         "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},
         "kernels_note": ("per-kernel CUDA-event times from a separate pass of the next two layers on one stream "

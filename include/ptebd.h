@@ -185,9 +185,10 @@ int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision);
  * small), which leaves the kept singular vectors orthogonal to about that
  * level; the truncated two-site state then carries a relative error of a few
  * 1e-5.  mode 1: the gated SVDs end with one more sweep at 2 sqrt(rows)
- * 2^-24, mode 2 (the default): the tSU SVDs as well, mode 0: none.  Measured
- * on one saturated layer with PtSU (N = 256, chi = 256) against the FP64 path:
- * 1 - F = 5.6e-7 (mode 0), 4.5e-7 (mode 1), 4.7e-8 (mode 2) for 9% more time. */
+ * 2^-24, mode 2 (the default): the tSU SVDs as well, mode 3: the tSU SVDs
+ * only, mode 0: none.  Measured on one saturated layer with PtSU (N = 256,
+ * chi = 256) against the FP64 path: 1 - F = 5.6e-7 (mode 0), 4.5e-7 (mode 1),
+ * 4.7e-8 (mode 2) for 9% more time.  PTEBD_ERR_INVALID for other modes. */
 int ptebd_set_svd_polish(ptebd_state* st, int32_t mode);
 
 /* Tensor cores for the gated bonds of a PTEBD_MIXED state (no counterpart in

@@ -49,7 +49,7 @@ struct ptebd_state {
     int jacobi_nw = 0;      // Jacobi block width (0: default; see ptebd_set_jacobi_width)
     int jacobi_pairs = 1;   // I columns per warp at width 16 (ptebd_set_jacobi_pairs)
     int tensor_cores = 1;   // complex64 theta' on the tensor cores (ptebd_set_tensor_cores)
-    int polish = 2;         // complex64 Jacobi polish sweep: 0 none, 1 gated SVDs, 2 gated and tSU
+    int polish = 2;         // complex64 Jacobi polish sweep: 0 none, 1 gated SVDs, 2 gated and tSU, 3 tSU
     cudaStream_t body_stream = nullptr;  // captures the bodies of the FP64 pass's IF nodes (owned)
     // set once a device error says that a CTA returned with its own bulk copies still in
     // flight (DERR_DRAIN): the state and its workspace can no longer be trusted, and
@@ -323,7 +323,7 @@ LayerArgs<R> stage_args(ptebd_state* st, bool gated) {
     a.nw = st->jacobi_nw;
     a.pairs = st->jacobi_pairs;
     a.tensor_cores = st->tensor_cores;
-    a.polish = (gated && st->polish >= 1) || (!gated && st->polish >= 2) ? 1 : 0;
+    a.polish = (gated && (st->polish == 1 || st->polish == 2)) || (!gated && st->polish >= 2) ? 1 : 0;
     a.wait_test = st->wait_test;
     a.bond_eps = at<double>(m, L.off_bond_eps);
     a.bond_nu = at<double>(m, L.off_bond_nu);
@@ -955,7 +955,7 @@ int ptebd_create(const ptebd_config* cfg, void* state_mem, size_t state_bytes, v
 }
 
 int ptebd_set_svd_polish(ptebd_state* st, int32_t mode) {
-    if (!st || mode < 0 || mode > 2) return set_err(st, PTEBD_ERR_INVALID, "polish mode must be 0, 1 or 2");
+    if (!st || mode < 0 || mode > 3) return set_err(st, PTEBD_ERR_INVALID, "polish mode must be 0, 1, 2 or 3");
     st->polish = mode;
     return PTEBD_OK;
 }

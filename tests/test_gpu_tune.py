@@ -118,3 +118,27 @@ def test_jacobi_pairs_rejects_other_values(ptebd):
     with pytest.raises(ptebd.PtebdError):
         st.set_jacobi_pairs(3)
     st.close()
+
+
+@pytest.mark.parametrize("mode", [0, 3])
+def test_polish_modes_match_oracle(ptebd, mode):
+    """Polish sweep off, or on the tSU SVDs only: the layer with its PtSU step
+    still matches the oracle to the mixed path's tolerance."""
+    n, chi, depth = 32, 64, 8
+    circuit = inputs.brickwork_circuit(53, n, depth)
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=1)
+    st.set_svd_polish(mode)
+    for parity, bonds, gates in circuit[:depth - 1]:
+        st.apply_layer(gates, parity)
+    ref = to_oracle(st)
+    load_into(st, ref)
+    parity, bonds, gates = circuit[depth - 1]
+    st.apply_layer(gates, parity)
+    oracle.apply_layer(ref, gates, parity, chi, 1e-12, g=1)
+    got = to_oracle(st)
+    for b in range(n - 1):
+        compare_spectra(got.lambdas[b], ref.lambdas[b], 1e-5, 1e-12, chi)
+    assert fidelity(got, ref) >= 1 - 1e-6
+    with pytest.raises(ptebd.PtebdError):
+        st.set_svd_polish(4)
+    st.close()

@@ -188,7 +188,9 @@ int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision);
  * 2^-24, mode 2 (the default): the tSU SVDs as well, mode 3: the tSU SVDs
  * only, mode 0: none.  Measured on one saturated layer with PtSU (N = 256,
  * chi = 256) against the FP64 path: 1 - F = 5.6e-7 (mode 0), 4.5e-7 (mode 1),
- * 4.7e-8 (mode 2) for 9% more time.  PTEBD_ERR_INVALID for other modes. */
+ * 4.7e-8 (mode 2) for 9% more time; at N = 1024, chi = 256: 3.2e-7 (mode
+ * 2), 1.7e-6 (mode 3, 4% faster), 4.9e-6 (mode 0).  PTEBD_ERR_INVALID for
+ * other modes. */
 int ptebd_set_svd_polish(ptebd_state* st, int32_t mode);
 
 /* Tensor cores for the gated bonds of a PTEBD_MIXED state (no counterpart in

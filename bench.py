@@ -97,6 +97,8 @@ def parse():
                    help="--serving: advance the states one by one (no batch graph), for comparison")
     p.add_argument("--no-tensor-cores", action="store_true",
                    help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
+    p.add_argument("--no-ptsu-shortcut", action="store_true",
+                   help="run the identity tSU half-step after parity-0 layers as well (for comparison)")
     p.add_argument("--svd-polish", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
                    help="complex64 polish sweep: 0 none, 1 gated, 2 gated and tSU, 3 tSU (-1: the library's choice)")
     p.add_argument("--jacobi-width", type=int, default=0, choices=[0, 8, 16],
@@ -243,6 +245,8 @@ def run_ours(args, rank, world, local_rank):
         st.set_chunk_streams(args.chunk_streams)
     if args.jacobi_width:
         st.set_jacobi_width(args.jacobi_width)
+    if args.no_ptsu_shortcut:
+        st.set_ptsu_shortcut(False)
     if args.svd_polish >= 0:
         st.set_svd_polish(args.svd_polish)
     if args.jacobi_pairs:
@@ -266,6 +270,7 @@ def run_ours(args, rank, world, local_rank):
     chi_now = st.chi()
     w0 = st.work_counters()
     gated = 0
+    tsu_stages = 0  # tSU half-steps the timed layers run (one fewer after a parity-0 layer with the shortcut)
     clocks = Clocks(smi_index(local_rank))
     barrier()
     torch.cuda.synchronize()
@@ -278,6 +283,7 @@ def run_ours(args, rank, world, local_rank):
         parity, bonds, _g = circuit[layer]
         st.apply_layer(dev_gates[layer], parity)
         gated += len(bonds)
+        tsu_stages += 2 * args.g - (1 if args.g and parity == 0 and not args.no_ptsu_shortcut else 0)
         layer += 1
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -323,8 +329,8 @@ def run_ours(args, rank, world, local_rank):
     # adds the chunks' eps sums
     n_chunks = args.chunk_streams or min(8, max(1, (n // 2) // 32))
     resolve = args.precision == "mixed"
-    per_layer = n_chunks * ((12 if resolve else 6) + 2 * (17 if resolve else 9) * args.g) + (1 if n_chunks > 1 else 0)
-    gpu_launches = args.steps * per_layer
+    gpu_launches = (n_chunks * (args.steps * (12 if resolve else 6) + tsu_stages * (17 if resolve else 9))
+                    + args.steps * (1 if n_chunks > 1 else 0))
 
     # ---- e2e: host gates (pinned) in, truncation metric out, through the C ABI
     e2e = None
@@ -374,7 +380,8 @@ def run_ours(args, rank, world, local_rank):
         "precision": args.precision,
         "prefill_layers": args.prefill, "max_chi_at_start": int(chi_now.max()),
         "gated_bonds_per_step": gated / args.steps,
-        "tsu_bonds_per_step": args.g * (n - 1),
+        "tsu_bonds_per_step": tsu_stages * (n - 1) / (2 * args.steps),
+        "ptsu_shortcut": not args.no_ptsu_shortcut,
         "chunk_streams": n_chunks,
         "jacobi_width": args.jacobi_width or "library choice",
         "svd_polish": args.svd_polish if args.svd_polish >= 0 else "library choice",
@@ -474,6 +481,8 @@ def fp64_at_headline(args, st, circuit, layer, local_rank):
     t0 = time.perf_counter()
     gam, lam = st.export()
     ref = ptebd.State(n, chi, "fp64", cutoff=1e-12, g=args.g)
+    if args.no_ptsu_shortcut:
+        ref.set_ptsu_shortcut(False)
     ref.load(gam, lam)
     del gam, lam
     setup_s = time.perf_counter() - t0

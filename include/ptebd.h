@@ -215,6 +215,19 @@ int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable);
  * the SVD's accuracy). */
 int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw);
 
+/* PtSU after a gated layer on bonds 0, 2, 4, ... (the paper's odd bonds; a
+ * PtSU step, Sec. III D, is tSU on those bonds and then on bonds 1, 3, 5,
+ * ...).  Right after such a layer every one of those bonds is in Schmidt form
+ * (Gamma_b = Lambda_{b-1}^-1 U, Gamma_{b+1} = V^dag Lambda_{b+1}^-1, the
+ * neighbouring Lambdas untouched), so the tSU two-site tensor there is
+ * U Lambda_b V^dag and the first half-step of the first PtSU step returns the
+ * state unchanged (up to rounding).  enable != 0 (the default): that half-step
+ * is left out of ptebd_apply_layer with g >= 1 and parity 0; enable = 0: it
+ * runs.  Layers of parity 1, explicit bond lists and ptebd_regauge always run
+ * every half-step.  No counterpart in the paper: a scheduling choice that
+ * drops an identity. */
+int ptebd_set_ptsu_shortcut(ptebd_state* st, int32_t enable);
+
 /* Columns of the complex64 Jacobi register block per warp at block width 16
  * (no counterpart in the paper: a scheduling choice).  pairs = 1 (the
  * default): 16 warps, one I column each, one column pair a round; pairs = 2:

@@ -48,6 +48,7 @@ struct ptebd_state {
     bool regauge64 = false; // PTEBD_MIXED: tSU stages run in FP64 (ptebd_set_regauge_precision)
     int jacobi_nw = 0;      // Jacobi block width (0: default; see ptebd_set_jacobi_width)
     int jacobi_pairs = 1;   // I columns per warp at width 16 (ptebd_set_jacobi_pairs)
+    int ptsu_shortcut = 1;  // leave out the identity half-step after a layer on bonds 0, 2, 4, ... (see run_layer)
     int tensor_cores = 1;   // complex64 theta' on the tensor cores (ptebd_set_tensor_cores)
     int polish = 2;         // complex64 Jacobi polish sweep: 0 none, 1 gated SVDs, 2 gated and tSU, 3 tSU
     cudaStream_t body_stream = nullptr;  // captures the bodies of the FP64 pass's IF nodes (owned)
@@ -583,8 +584,20 @@ int run_layer(ptebd_state* st, const Stage* gated_stage, int g) {
     const int32_t* lists = at<int32_t>(st->mem, L.off_bonds);
     std::vector<Stage> stages;
     if (gated_stage && gated_stage->nb > 0) stages.push_back(*gated_stage);
+    // A PtSU step is tSU on bonds 0, 2, 4, ... (the paper's odd bonds) then on
+    // bonds 1, 3, 5, ....  Right after a gated layer on every bond of parity 0,
+    // each of those bonds is in Schmidt form: Gamma_b = Lambda_{b-1}^-1 U and
+    // Gamma_{b+1} = V^dag Lambda_{b+1}^-1 with Lambda_b the kept values, and the
+    // neighbouring Lambdas are untouched by the layer, so the tSU two-site tensor
+    // is U Lambda_b V^dag: its SVD returns the same U, Lambda_b, V (all kept
+    // values lie above the cutoff), and the first half-step of the first PtSU
+    // step leaves the state as it is.  It is left out (ptebd_set_ptsu_shortcut).
+    const bool identity_half = st->ptsu_shortcut && gated_stage && gated_stage->nb > 0 &&
+                               gated_stage->h_list == nullptr && gated_stage->parity == 0 &&
+                               gated_stage->nb == n_parity_bonds(L.n_sites, 0);
     for (int step = 0; step < g; ++step) {
-        stages.push_back(Stage{lists, nullptr, 0, n_parity_bonds(L.n_sites, 0), nullptr, false});
+        if (!(step == 0 && identity_half))
+            stages.push_back(Stage{lists, nullptr, 0, n_parity_bonds(L.n_sites, 0), nullptr, false});
         stages.push_back(Stage{lists + L.max_bonds, nullptr, 1, n_parity_bonds(L.n_sites, 1), nullptr, false});
     }
     if (stages.empty()) return PTEBD_OK;
@@ -970,6 +983,12 @@ int ptebd_set_jacobi_width(ptebd_state* st, int32_t nw) {
     if (!st) return PTEBD_ERR_INVALID;
     if (nw != 0 && nw != 8 && nw != 16) return set_err(st, PTEBD_ERR_INVALID, "Jacobi block width must be 0, 8 or 16");
     st->jacobi_nw = nw;
+    return PTEBD_OK;
+}
+
+int ptebd_set_ptsu_shortcut(ptebd_state* st, int32_t enable) {
+    if (!st) return PTEBD_ERR_INVALID;
+    st->ptsu_shortcut = enable ? 1 : 0;
     return PTEBD_OK;
 }
 

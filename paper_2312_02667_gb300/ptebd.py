@@ -39,7 +39,7 @@ EXPORTS = (
     "ptebd_batch_create", "ptebd_batch_destroy", "ptebd_batch_last_error", "ptebd_batch_apply_layer",
     "ptebd_svd_batched_noalloc", "ptebd_canonicalize", "ptebd_sample", "ptebd_sample_workspace_bytes",
     "ptebd_set_chunk_streams", "ptebd_test_wait_timeout", "ptebd_alu_peak", "ptebd_set_regauge_precision",
-    "ptebd_set_jacobi_width", "ptebd_set_jacobi_pairs", "ptebd_autotune", "ptebd_set_tensor_cores",
+    "ptebd_set_jacobi_width", "ptebd_set_jacobi_pairs", "ptebd_set_ptsu_shortcut", "ptebd_autotune", "ptebd_set_tensor_cores",
     "ptebd_set_svd_polish",
 )
 KERNEL_KINDS = ("theta", "svd", "truncate", "gamma", "reduce", "factor", "resolve")
@@ -108,6 +108,7 @@ _SIGS = {
     "ptebd_set_regauge_precision": (_P, ctypes.c_int32),
     "ptebd_set_jacobi_width": (_P, ctypes.c_int32),
     "ptebd_set_jacobi_pairs": (_P, ctypes.c_int32),
+    "ptebd_set_ptsu_shortcut": (_P, ctypes.c_int32),
     "ptebd_set_tensor_cores": (_P, ctypes.c_int32),
     "ptebd_set_svd_polish": (_P, ctypes.c_int32),
     "ptebd_autotune": (_P, _D, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t, _D),
@@ -347,6 +348,10 @@ def ptebd_set_jacobi_width(h, nw):
 
 def ptebd_set_jacobi_pairs(h, pairs):
     _check(lib.ptebd_set_jacobi_pairs(h, int(pairs)), h)
+
+
+def ptebd_set_ptsu_shortcut(h, enable):
+    _check(lib.ptebd_set_ptsu_shortcut(h, 1 if enable else 0), h)
 
 
 def ptebd_autotune(h, gates, parity, scratch_ptr, scratch_bytes):
@@ -621,6 +626,9 @@ class State:
 
     def set_jacobi_pairs(self, pairs):
         ptebd_set_jacobi_pairs(self.handle, pairs)
+
+    def set_ptsu_shortcut(self, enable):
+        ptebd_set_ptsu_shortcut(self.handle, enable)
 
     def set_tensor_cores(self, enable):
         ptebd_set_tensor_cores(self.handle, enable)

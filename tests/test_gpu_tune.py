@@ -142,3 +142,46 @@ def test_polish_modes_match_oracle(ptebd, mode):
     with pytest.raises(ptebd.PtebdError):
         st.set_svd_polish(4)
     st.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ptsu_shortcut_leaves_the_state_as_the_full_step(ptebd, prec):
+    """After a layer on bonds 0, 2, 4, ... the first tSU half-step is the
+    identity: with it left out (the default) the state after the layer and its
+    PtSU steps matches the oracle, which runs every half-step, and the run with
+    it; a parity-1 layer runs every half-step either way (bit-identical)."""
+    n, chi, depth = 32, 64, 8
+    circuit = inputs.brickwork_circuit(59, n, depth)
+    tol, ftol = (1e-10, 1e-9) if prec == "fp64" else (1e-5, 1e-6)
+    runs = {}
+    for shortcut in (True, False):
+        st = ptebd.State(n, chi, prec, cutoff=1e-12, g=2)
+        st.set_ptsu_shortcut(shortcut)
+        for parity, bonds, gates in circuit[:depth - 2]:
+            st.apply_layer(gates, parity)
+        ref = to_oracle(st)
+        for parity, bonds, gates in circuit[depth - 2:]:
+            load_into(st, ref)
+            st.apply_layer(gates, parity)
+            oracle.apply_layer(ref, gates, parity, chi, 1e-12, g=2)
+            got = to_oracle(st)
+            for b in range(n - 1):
+                compare_spectra(got.lambdas[b], ref.lambdas[b], tol, 1e-12, chi)
+            assert fidelity(got, ref) >= 1 - ftol
+        runs[shortcut] = to_oracle(st)
+        st.close()
+    assert fidelity(runs[True], runs[False]) >= 1 - ftol
+    # a parity-1 layer: the same launches with or without the shortcut
+    start = runs[True]
+    parity, bonds, gates = circuit[5]
+    assert parity == 1
+    snaps = []
+    for shortcut in (True, False):
+        st = ptebd.State(n, chi, prec, cutoff=1e-12, g=1)
+        st.set_ptsu_shortcut(shortcut)
+        load_into(st, start)
+        st.apply_layer(gates, parity)
+        snaps.append(snapshot(st))
+        st.close()
+    assert all(np.array_equal(a, b) for a, b in zip(snaps[0][0], snaps[1][0]))
+    assert all(np.array_equal(a, b) for a, b in zip(snaps[0][1], snaps[1][1]))

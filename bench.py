@@ -41,7 +41,8 @@ SM_COUNT = 152
 # `achieved` is timed on; dram__bytes_read.sum + dram__bytes_write.sum of the
 # three Jacobi launches of one step, the gated SVDs and the two tSU passes on
 # M^dag: 291.2, 39.3, 28.9 GB at the first key, 315.8, 45.5, 35.3 GB at the
-# second, 315.7, 45.5, 35.3 GB at the third; averaged per launch), keyed by the SHA-256 of
+# second, 315.7, 45.5, 35.3 GB at the third and 315.8, 45.5, 35.3 GB at the
+# fourth; averaged per launch), keyed by the SHA-256 of
 # the kernel source it was taken on, with comments and blank lines removed (a
 # comment edit leaves the key alone).  Any other code reports null: the
 # counters no longer describe the kernel.
@@ -49,6 +50,7 @@ JACOBI_TRAFFIC = {
     "a673d11c5d5a93dc1bb29eacc0981c712ff478a81a49b8f0917de1ae980a5fa0": 359.46e9 / 3,
     "67f5d33a0c769e2e0fea0fd8d30e312096ce4418525e18a236e430e26c66bc0b": 396.6e9 / 3,
     "a9c859b525d94476efa21326b5bbd6f6759842cca47e2da411c8f315a9ccf676": 396.57e9 / 3,
+    "5491b7d858d3e01f7faed505b83a18a716618e41f84acfa5cb01c875475892d9": 396.59e9 / 3,
 }
 
 

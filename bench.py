@@ -409,7 +409,8 @@ def run_ours(args, rank, world, local_rank):
             "unit": "TFLOP/s",
             "frac": svd_rate / peak if peak else None,
             "traffic": jacobi_traffic() if args.precision == "mixed" and args.n_sites == 1024 and args.chi == 256 else None,
-            "traffic_note": "bytes per launch, averaged over the step's three Jacobi launches (gated 512x512 + two tSU passes on M^dag); "
+            "traffic_note": "bytes per launch, averaged over the three Jacobi launches of a step that runs every PtSU half-step "
+                            "(gated 512x512 + two tSU passes on M^dag; ncu capture with --no-ptsu-shortcut --chunk-streams 1); "
                             "the blocked Jacobi streams every matrix past its register-resident 16-column block "
                             "nb(nb-1)/2 times per sweep, and 152 concurrent 2 MB matrices exceed L2",
             "algorithmic": "28 flop per column-pair-row visit x sweeps x n(n-1)/2 x m, counted on the device",

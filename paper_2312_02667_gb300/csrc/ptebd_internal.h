@@ -106,7 +106,7 @@ struct LayerArgs {
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
     int nw;           // Jacobi block width requested (0: the default; 8 or 16 for complex64)
     int pairs;        // complex64, width 16: I columns per warp (1: 16 warps; 2: 8 warps, two pairs a round)
-    int tensor_cores; // complex64 theta' and the Gamma GEMM of gated bonds on the tensor cores
+    int tensor_cores; // complex64 theta', the Gamma GEMM and the tSU projection on the tensor cores
                       // (tcgen05, 3xTF32) when chip >= 64
     int polish;       // complex64 Jacobi: one last sweep at the tighter threshold (see Eps::polish)
     int mode;         // 0: gated bond; 1: tSU through the rank-chi_b factorisation
@@ -132,6 +132,7 @@ template <typename R> cudaError_t launch_jacobi(const LayerArgs<R>& a, cudaStrea
 // theta' of a complex64 state on the tensor cores (ptebd_theta_tc.cu)
 cudaError_t launch_theta_tc(const LayerArgs<float>& a, cudaStream_t s);
 cudaError_t launch_gamma_gemm_tc(const LayerArgs<float>& a, cudaStream_t s);  // the GEMM factor of the Gamma rebuild
+cudaError_t launch_proj_tc(const LayerArgs<float>& a, cudaStream_t s);        // M^dag of the tSU factorisation
 cudaError_t theta_tc_prepare();  // raises the smem limits of both tensor-core kernels
 template <typename R> cudaError_t launch_truncate(const LayerArgs<R>& a, cudaStream_t s);
 template <typename R, typename G = cx_t<R>> cudaError_t launch_gamma(const LayerArgs<R>& a, cudaStream_t s);

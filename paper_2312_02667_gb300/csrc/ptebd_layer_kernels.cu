@@ -754,12 +754,8 @@ __global__ void k_add_partials(const double* partials, int k, double* totals) {
 
 // -------------------------------------------------------------- launchers --
 template <typename R, typename G> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
-    // Tensor cores for the gated stage only: their FP32 accumulation shrinks
-    // every sum by a few 1e-8 relative, which the Schmidt reading renormalises
-    // away after a gate but which would build up over the chain of tSU steps
-    // (they keep S as it is).
     if constexpr (std::is_same<R, float>::value)
-        if (a.tensor_cores && a.mode == 0 && a.chip >= 64 && a.refine == 0) return launch_theta_tc(a, s);
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_theta_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 grid(tiles, tiles, a.count);
     k_theta<R, G><<<grid, 256, 0, s>>>(a);
@@ -776,7 +772,7 @@ template <typename R, typename G> cudaError_t launch_gamma(const LayerArgs<R>& a
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<R, float>::value)
-        if (a.tensor_cores && a.mode == 0 && a.chip >= 64 && a.refine == 0) return launch_gamma_gemm_tc(a, s);
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_gamma_gemm_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 g2(tiles, tiles, 2 * a.count);
     k_gamma_gemm<R, G><<<g2, 256, 0, s>>>(a);
@@ -789,6 +785,8 @@ template <typename R, typename G> cudaError_t launch_xform(const LayerArgs<R>& a
     return cudaGetLastError();
 }
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
+    if constexpr (std::is_same<R, float>::value)
+        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_proj_tc(a, s);
     dim3 grid((2 * a.chip + 31) / 32, (a.chip + 31) / 32, a.count);
     k_proj<R><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();

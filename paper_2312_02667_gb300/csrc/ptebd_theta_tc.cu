@@ -216,18 +216,35 @@ __device__ __forceinline__ void tc_end(uint32_t tmem) {
 // work.  One thread issues the chunk's 24 MMAs (3xTF32 for the real and the
 // imaginary part, 4 K steps of 8 FP32 values: hi*hi into the accumulators at
 // columns 0 and 128, the cross terms into the corrections at 256 and 384) and
-// commits them to the
-// stage's mbarrier, which the threads wait on before they refill that stage.
-// Returns false when a wait ran out (the accumulators cannot be trusted then).
+// commits them to the stage's mbarrier, which the threads wait on before they
+// refill that stage.
+//
+// The accumulators start afresh every kFlush chunks: at the end of such a group
+// the threads wait for its MMAs and add main + correction into FP32 sums held
+// in registers (round to nearest).  The tensor cores' accumulation rounds
+// toward zero (about 2.5e-8 relative per K step, always shrinking), so a sum
+// over the whole K dimension would shrink by that much per step (1.6e-6 at
+// K = 256 complex); over a group of 8 K steps it is 2e-7, and adding the groups
+// in registers adds no bias.  sum[c] of a thread: TMEM lane (row) 32 (warp & 3)
+// + lane, column c of the real (warps 0-3) or imaginary (warps 4-7) result.
+// Returns false when a wait ran out (the sums cannot be trusted then).
+constexpr int kFlush = 2;
 template <typename Fetch, typename Put>
-__device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int nk, Fetch&& fetch, Put&& put) {
+__device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int nk, float (&sum)[128], Fetch&& fetch,
+                            Put&& put) {
     const uint32_t d_re = tmem, d_im = tmem + 128, c_re = tmem + 256, c_im = tmem + 384;
+    const int warp = threadIdx.x >> 5, kind = warp >> 2;
+    const uint32_t lanes = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(kind * 128);
+#pragma unroll
+    for (int c = 0; c < 128; ++c) sum[c] = 0.f;
     float2 ra[8], rb[8];
     if (nk > 0) fetch(0, ra, rb);
     bool ok = true;
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc & 1;
         unsigned char* S = sm + st * kStage;
+        // (a flush already waited for chunk kc - 2 when it ended a group: the
+        // phase is complete and the wait returns at once)
         if (kc >= 2 && !tc_mbar_wait(&bar[st], (uint32_t)((kc - 2) >> 1) & 1u)) ok = false;
         if (!__syncthreads_and(ok)) { ok = false; break; }
         put(S, ra, rb);
@@ -243,7 +260,7 @@ __device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int
                 const uint64_t ah = sdesc_sw128(base + off), al = sdesc_sw128(base + kTile + off);
                 const uint64_t rh = sdesc_sw128(base + 2 * kTile + off), rl = sdesc_sw128(base + 3 * kTile + off);
                 const uint64_t ih = sdesc_sw128(base + 4 * kTile + off), il = sdesc_sw128(base + 5 * kTile + off);
-                const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                const uint32_t acc = (kc % kFlush != 0 || ks > 0) ? 1u : 0u;
                 mma_tf32(d_re, ah, rh, kIdesc, acc);
                 mma_tf32(c_re, ah, rl, kIdesc, acc);
                 mma_tf32(c_re, al, rh, kIdesc, 1u);
@@ -253,11 +270,33 @@ __device__ bool tc_pipeline(unsigned char* sm, uint64_t* bar, uint32_t tmem, int
             }
             mma_commit(&bar[st]);
         }
+        if (kc % kFlush == kFlush - 1 || kc == nk - 1) {
+            if (!tc_mbar_wait(&bar[st], (uint32_t)(kc >> 1) & 1u)) ok = false;
+            if (!__syncthreads_and(ok)) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int cb = 0; cb < 8; ++cb) {
+                float v[16], c[16];
+                tmem_ld16(lanes + (uint32_t)(16 * cb), v);
+                tmem_ld16(lanes + 256u + (uint32_t)(16 * cb), c);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) sum[16 * cb + i] += v[i] + c[i];
+            }
+            tc_fence_before();
+            __syncthreads();  // the next group's first MMAs overwrite the accumulators
+        }
     }
-    if (ok && nk > 0 && !tc_mbar_wait(&bar[(nk - 1) & 1], (uint32_t)((nk - 1) >> 1) & 1u)) ok = false;
-    ok = __syncthreads_and(ok);
-    tc_fence_after();
     return ok;
+}
+
+// The sums of tc_pipeline into shared memory: re[c * kThPitch + r] and
+// im[c * kThPitch + r] for the 128 x 128 tile (rows r = TMEM lanes).
+__device__ __forceinline__ void stage_sums(const float (&sum)[128], float* re, float* im) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = 32 * (warp & 3) + lane;
+    float* dst = (warp >> 2) ? im : re;
+#pragma unroll
+    for (int c = 0; c < 128; ++c) dst[c * kThPitch + row] = sum[c];
 }
 
 // grid (chip / 64, chip / 64, count), 256 threads, kTcSmem bytes of dynamic smem.
@@ -276,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(LayerArgs<float> a) 
     const int j = blockIdx.z;
     const int b = a.bonds[j];
     const int chip = a.chip;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     if (b < 0 || b > a.n_sites - 2 || a.chi[b] < 1 || a.chi[b] > chip || a.chi[b + 1] < 1 ||
         a.chi[b + 1] > chip || a.chi[b + 2] < 1 || a.chi[b + 2] > chip) {
         if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
@@ -319,11 +358,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(LayerArgs<float> a) 
     }
     const uint32_t tmem = tc_begin(bar, tmem_slot);
     const int nk = (cm + 15) / 16;  // K chunks of 16 complex values
+    float sum[128];
     // element i of a thread: A (r = e & 127, kk = e >> 7), B (kk = e & 15, n = e >> 4), e = tid + 256 i;
     // fetch loads and scales (A: X_s = Lambda_{b-1} Gamma_b^s Lambda_b; B: Y_t = Gamma_{b+1}^t Lambda_{b+1}),
     // put splits and stores (B_re rows (Re y, -Im y), B_im rows (Im y, Re y))
     const bool ok = tc_pipeline(
-        sm, bar, tmem, nk,
+        sm, bar, tmem, nk, sum,
         [&](int kc, float2 (&ra)[8], float2 (&rb)[8]) {
             float2 ga[8], gb[8];
 #pragma unroll
@@ -365,21 +405,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_theta_tc(LayerArgs<float> a) 
         tc_end(tmem);
         return;
     }
-    // ---- epilogue: accumulators -> shared memory (column-major, pitch 129)
+    // ---- epilogue: the sums -> shared memory (column-major, pitch 129)
     float* th_re = reinterpret_cast<float*>(sm);
     float* th_im = th_re + 128 * kThPitch;
-    {
-        const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
-        float* dst = half ? th_im : th_re;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 16) {
-            float v[16], c[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * 128 + c0), v);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(256 + half * 128 + c0), c);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) dst[(c0 + i) * kThPitch + row] = v[i] + c[i];
-        }
-    }
+    stage_sums(sum, th_re, th_im);
     tc_end(tmem);
     // ---- gate mix and stores: theta_{st}(alpha, gamma) at column t * 64 + gamma, row s * 64 + alpha
     const size_t ldw = a.ldw;
@@ -506,9 +535,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gamma_tc(LayerArgs<float> a) 
     }
     const uint32_t tmem = tc_begin(bar, tmem_slot);  // its barrier also publishes pcol .. qscl
     const int nk = (rows + 15) / 16;
+    float sum[128];
     // element i of a thread: e = tid + 256 i, kk = e & 15 (K = row r of P and Q), row e >> 4 of A and of B
     const bool ok = tc_pipeline(
-        sm, bar, tmem, nk,
+        sm, bar, tmem, nk, sum,
         [&](int kc, float2 (&ra)[8], float2 (&rb)[8]) {
             float2 pa[8], qb[8];
 #pragma unroll
@@ -539,21 +569,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gamma_tc(LayerArgs<float> a) 
         return;
     }
     const double* lnb = a.lam + (size_t)(tall ? b + 2 : b) * chip;  // Lambda_{b+1} or Lambda_{b-1}
+    float* zr = reinterpret_cast<float*>(sm);
+    float* zi = zr + 128 * kThPitch;
+    stage_sums(sum, zr, zi);
+    __syncthreads();
     {
         const int q = warp & 3, half = warp >> 2;
         const int row = r0 + 32 * q + lane;
 #pragma unroll 1
         for (int cc = 0; cc < 64; cc += 16) {
             const int cl0 = half * 64 + cc;
-            float vre[16], vim[16], cre[16], cim[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)cl0, vre);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 128u + (uint32_t)cl0, vim);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256u + (uint32_t)cl0, cre);
-            tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 384u + (uint32_t)cl0, cim);
+            float vre[16], vim[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                vre[i] += cre[i];
-                vim[i] += cim[i];
+                vre[i] = zr[(cl0 + i) * kThPitch + 32 * q + lane];
+                vim[i] = zi[(cl0 + i) * kThPitch + 32 * q + lane];
             }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -573,12 +603,102 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gamma_tc(LayerArgs<float> a) 
     tc_end(tmem);
 }
 
+// ---------------------------------------------------------- tSU projection --
+// M^dag = theta^dag U_X (the second tSU matrix, Sec. III D), the product of
+// k_proj on the tensor cores: out[r, c] = sum_k A[r, k] B[k, c] / sigma_X[c]
+// with A = theta^dag (rows 2 chi_{b+1}, K = 2 chi_{b-1}) in w0 and B = U_X
+// Sigma_X (K x chi_b) in w; a zero sigma_X gives a zero column.  A CTA computes
+// a 128 x 128 tile of out (w1).
+// grid (ceil(2 chip / 128), ceil(chip / 128), count), 256 threads, kTcSmem bytes.
+__global__ void __launch_bounds__(kTcThreads, 1) k_proj_tc(LayerArgs<float> a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * kStage);  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+    float* bscl = reinterpret_cast<float*>(sm + 2 * kStage + 64);  // [128]
+
+    const int j = blockIdx.z;
+    const int32_t* d = a.dims + j * kDims;
+    const int cl = d[D_CL], cm = d[D_CM], cr = d[D_CR];
+    const int rows = 2 * cr, kdim = 2 * cl;
+    const int r0 = blockIdx.x * 128, c0 = blockIdx.y * 128;
+    if (r0 >= rows || c0 >= cm) return;  // uniform over the CTA, before any allocation
+    const size_t ldw = a.ldw;
+    const float2* A = a.w0 + (size_t)j * ldw * ldw;
+    const float2* B = a.w + (size_t)j * ldw * ldw;
+    float2* out = a.w1 + (size_t)j * ldw * ldw;
+    const double* sig = a.norms + (size_t)j * ldw;
+    const int tid = threadIdx.x;
+    if (tid < 128) {
+        const int gc = c0 + tid;
+        const double sg = gc < cm ? sig[gc] : 0.0;
+        bscl[tid] = sg > 0.0 ? (float)(1.0 / sg) : 0.f;
+    }
+    const uint32_t tmem = tc_begin(bar, tmem_slot);  // its barrier also publishes bscl
+    const int nk = (kdim + 15) / 16;
+    float sum[128];
+    // element i of a thread: A (row e & 127 = output row, kk = e >> 7), B (kk = e & 15, row e >> 4), e = tid + 256 i
+    const bool ok = tc_pipeline(
+        sm, bar, tmem, nk, sum,
+        [&](int kc, float2 (&ra)[8], float2 (&rb)[8]) {
+            float2 xb[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int e = tid + kTcThreads * i;
+                const int gr = r0 + (e & 127), gk = kc * 16 + (e >> 7);
+                ra[i] = (gr < rows && gk < kdim) ? A[(size_t)gk * ldw + gr] : make_float2(0.f, 0.f);
+                const int gc = c0 + (e >> 4), gk2 = kc * 16 + (e & 15);
+                xb[i] = (gc < cm && gk2 < kdim) ? B[(size_t)gc * ldw + gk2] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = (tid + kTcThreads * i) >> 4;
+                rb[i] = make_float2(xb[i].x * bscl[c], xb[i].y * bscl[c]);
+            }
+        },
+        [&](unsigned char* S, const float2 (&ra)[8], const float2 (&rb)[8]) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {  // A B: B_re rows (Re b, -Im b), B_im rows (Im b, Re b)
+                const int e = tid + kTcThreads * i;
+                put_a(S, e & 127, e >> 7, ra[i]);
+                put_b(S, e >> 4, e & 15, make_float2(rb[i].x, -rb[i].y), make_float2(rb[i].y, rb[i].x));
+            }
+        });
+    if (!ok) {
+        if (tid == 0) atomicOr(a.err, DERR_TIMEOUT | DERR_DRAIN);
+        tc_end(tmem);
+        return;
+    }
+    float* zr = reinterpret_cast<float*>(sm);
+    float* zi = zr + 128 * kThPitch;
+    stage_sums(sum, zr, zi);
+    __syncthreads();
+    {
+        // column by column: 256 threads write rows r0 .. r0 + 127 of two columns at a time
+        const int r = tid & 127;
+        const int gr = r0 + r;
+#pragma unroll 1
+        for (int cc = tid >> 7; cc < 128; cc += 2) {
+            const int gc = c0 + cc;
+            if (gr < rows && gc < cm) out[(size_t)gc * ldw + gr] = make_float2(zr[cc * kThPitch + r], zi[cc * kThPitch + r]);
+        }
+    }
+    tc_end(tmem);
+}
+
 }  // namespace
 
 cudaError_t theta_tc_prepare() {
     cudaError_t e = cudaFuncSetAttribute(k_theta_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gamma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_proj_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     return e;
+}
+
+cudaError_t launch_proj_tc(const LayerArgs<float>& a, cudaStream_t s) {
+    dim3 grid((2 * a.chip + 127) / 128, (a.chip + 127) / 128, a.count);
+    k_proj_tc<<<grid, kTcThreads, kTcSmem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gamma_gemm_tc(const LayerArgs<float>& a, cudaStream_t s) {

@@ -193,18 +193,19 @@ int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision);
  * other modes. */
 int ptebd_set_svd_polish(ptebd_state* st, int32_t mode);
 
-/* Tensor cores for the gated bonds of a PTEBD_MIXED state (no counterpart in
- * the paper: a choice of arithmetic unit).  enable != 0 (the default): when
- * chi_max rounded up (16 * 2^k) is at least 64, theta' = U theta and the GEMM
- * factor of the Gamma rebuild of a gated bond are formed by tcgen05.mma
- * kind::tf32 with FP32 accumulation in tensor memory, operands split as hi +
- * lo TF32 pairs and multiplied hi*hi + hi*lo + lo*hi (FP32 accuracy), the
- * cross terms in accumulators of their own; enable = 0: FP32 FMAs on the CUDA
- * cores.  The two round differently (both to FP32 accuracy).  The tSU steps
- * always run on the CUDA cores: the tensor cores' FP32 accumulation shrinks
- * sums by a few 1e-8 relative, which the Schmidt reading of a gated bond
- * renormalises away but which a chain of tSU steps (S kept as it is) would
- * accumulate.  No effect on PTEBD_FP64 states. */
+/* Tensor cores for a PTEBD_MIXED state (no counterpart in the paper: a
+ * choice of arithmetic unit).  enable != 0 (the default): when chi_max
+ * rounded up (16 * 2^k) is at least 64, theta' = U theta, the GEMM factor of
+ * the Gamma rebuild and the tSU projection M^dag = theta^dag U_X are formed by
+ * tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory, operands
+ * split as hi + lo TF32 pairs and multiplied hi*hi + hi*lo + lo*hi (FP32
+ * accuracy), the cross terms in accumulators of their own.  The tensor cores'
+ * accumulation rounds toward zero (sums shrink by about 2.5e-8 relative per K
+ * step of 8); the accumulators therefore restart every 2 K chunks of 16
+ * complex values and the partial results are added in FP32 registers with
+ * round-to-nearest, which bounds the shrinkage at about 2e-7 relative whatever
+ * chi is.  enable = 0: FP32 FMAs on the CUDA cores.  The two round
+ * differently (both to FP32 accuracy).  No effect on PTEBD_FP64 states. */
 int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable);
 
 /* Jacobi block width of the handle's SVDs (no counterpart in the paper: a

@@ -72,3 +72,9 @@ def test_reference_arm_prints_on_rank_zero_only():
     line = json.loads(out[0].splitlines()[-1])
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same workload description as the GPU arm's line (bench.headline_config)
+    sys.path.insert(0, ROOT)
+    import bench
+    import argparse
+    args = argparse.Namespace(n_sites=32, chi=16, g=1, gpus=1)
+    assert line["config"] == bench.headline_config(args, 1)

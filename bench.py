@@ -97,6 +97,8 @@ def parse():
                    help="--serving: the first K of the 64 seeded circuits (for the slow FP64 pass)")
     p.add_argument("--serial", action="store_true",
                    help="--serving: advance the states one by one (no batch graph), for comparison")
+    p.add_argument("--tsu-tensor-cores", action="store_true",
+                   help="the tSU steps on the tensor cores as well (ptebd_set_tensor_cores mode 2)")
     p.add_argument("--no-tensor-cores", action="store_true",
                    help="complex64 contractions on the CUDA cores instead of tcgen05 (for comparison)")
     p.add_argument("--no-ptsu-shortcut", action="store_true",
@@ -243,6 +245,8 @@ def run_ours(args, rank, world, local_rank):
     st = ptebd.State(n, chi, args.precision, cutoff=1e-12, g=args.g, resolve=args.resolve)
     if args.no_tensor_cores:
         st.set_tensor_cores(False)
+    elif args.tsu_tensor_cores:
+        st.set_tensor_cores(2)
     if args.chunk_streams:
         st.set_chunk_streams(args.chunk_streams)
     if args.jacobi_width:
@@ -386,6 +390,7 @@ def run_ours(args, rank, world, local_rank):
         "ptsu_shortcut": not args.no_ptsu_shortcut,
         "chunk_streams": n_chunks,
         "jacobi_width": args.jacobi_width or "library choice",
+        "tensor_cores": "off" if args.no_tensor_cores else ("gated and tSU" if args.tsu_tensor_cores else "gated stages"),
         "svd_polish": args.svd_polish if args.svd_polish >= 0 else "library choice",
         "jacobi_columns_per_warp": args.jacobi_pairs or "library choice",
         "kernels_ms_per_step": {k: v[0] / diag_layers for k, v in kern.items()},

@@ -194,18 +194,23 @@ int ptebd_set_regauge_precision(ptebd_state* st, int32_t precision);
 int ptebd_set_svd_polish(ptebd_state* st, int32_t mode);
 
 /* Tensor cores for a PTEBD_MIXED state (no counterpart in the paper: a
- * choice of arithmetic unit).  enable != 0 (the default): when chi_max
- * rounded up (16 * 2^k) is at least 64, theta' = U theta, the GEMM factor of
- * the Gamma rebuild and the tSU projection M^dag = theta^dag U_X are formed by
+ * choice of arithmetic unit).  When chi_max rounded up (16 * 2^k) is at
+ * least 64, enable = 1 (the default; any value other than 0 and 2): theta' =
+ * U theta and the GEMM factor of the Gamma rebuild of gated bonds are formed by
  * tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory, operands
  * split as hi + lo TF32 pairs and multiplied hi*hi + hi*lo + lo*hi (FP32
- * accuracy), the cross terms in accumulators of their own.  The tensor cores'
- * accumulation rounds toward zero (sums shrink by about 2.5e-8 relative per K
- * step of 8); the accumulators therefore restart every 2 K chunks of 16
- * complex values and the partial results are added in FP32 registers with
- * round-to-nearest, which bounds the shrinkage at about 2e-7 relative whatever
- * chi is.  enable = 0: FP32 FMAs on the CUDA cores.  The two round
- * differently (both to FP32 accuracy).  No effect on PTEBD_FP64 states. */
+ * accuracy), the cross terms in accumulators of their own; enable = 2: the
+ * tSU steps' theta, projection M^dag = theta^dag U_X and Gamma GEMM as well;
+ * enable = 0: FP32 FMAs on the CUDA cores.  The tensor cores' accumulation
+ * rounds toward zero (sums shrink by about 2.5e-8 relative per K step of 8);
+ * the accumulators restart every 2 K chunks of 16 complex values and the
+ * partial results are added in FP32 registers with round-to-nearest, which
+ * bounds the shrinkage at about 2e-7 relative per product whatever chi is.  A
+ * gated bond's Schmidt reading renormalises it away; a tSU step keeps S as it
+ * is, and over the bonds of one PtSU step at N = 1024, chi = 256 it moved the
+ * norm of the state by 5.4e-4 (mode 2), hence mode 1 as the default.  The
+ * tensor-core and CUDA-core paths round differently (both to FP32 accuracy).
+ * No effect on PTEBD_FP64 states. */
 int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable);
 
 /* Jacobi block width of the handle's SVDs (no counterpart in the paper: a

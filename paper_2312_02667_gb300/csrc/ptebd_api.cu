@@ -975,7 +975,7 @@ int ptebd_set_svd_polish(ptebd_state* st, int32_t mode) {
 
 int ptebd_set_tensor_cores(ptebd_state* st, int32_t enable) {
     if (!st) return PTEBD_ERR_INVALID;
-    st->tensor_cores = enable ? 1 : 0;
+    st->tensor_cores = enable == 2 ? 2 : (enable ? 1 : 0);
     return PTEBD_OK;
 }
 

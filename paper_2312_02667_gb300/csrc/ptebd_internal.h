@@ -106,8 +106,8 @@ struct LayerArgs {
                       // reaches, with a short limit, so the CTA aborts and latches DERR_TIMEOUT
     int nw;           // Jacobi block width requested (0: the default; 8 or 16 for complex64)
     int pairs;        // complex64, width 16: I columns per warp (1: 16 warps; 2: 8 warps, two pairs a round)
-    int tensor_cores; // complex64 theta', the Gamma GEMM and the tSU projection on the tensor cores
-                      // (tcgen05, 3xTF32) when chip >= 64
+    int tensor_cores; // complex64 on the tensor cores (tcgen05, 3xTF32) when chip >= 64: 1 theta' and
+                      // the Gamma GEMM of gated stages, 2 the tSU steps as well
     int polish;       // complex64 Jacobi: one last sweep at the tighter threshold (see Eps::polish)
     int mode;         // 0: gated bond; 1: tSU through the rank-chi_b factorisation
     int pass;         // Jacobi: 0 = rows/cols from dims, 1 = the X factor (2 chi_{b-1} x chi_b)

@@ -754,8 +754,13 @@ __global__ void k_add_partials(const double* partials, int k, double* totals) {
 
 // -------------------------------------------------------------- launchers --
 template <typename R, typename G> cudaError_t launch_theta(const LayerArgs<R>& a, cudaStream_t s) {
+    // tensor_cores 1: gated stages; 2: the tSU steps as well.  On a tSU step the
+    // accumulation's residual shrinkage (about 2e-7 per product) is not
+    // renormalised away, and over the bonds of a PtSU step it moves the norm of
+    // the state: 5.4e-4 at N = 1024, chi = 256.
     if constexpr (std::is_same<R, float>::value)
-        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_theta_tc(a, s);
+        if (a.tensor_cores && (a.mode == 0 || a.tensor_cores == 2) && a.chip >= 64 && a.refine == 0)
+            return launch_theta_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 grid(tiles, tiles, a.count);
     k_theta<R, G><<<grid, 256, 0, s>>>(a);
@@ -772,7 +777,8 @@ template <typename R, typename G> cudaError_t launch_gamma(const LayerArgs<R>& a
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if constexpr (std::is_same<R, float>::value)
-        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_gamma_gemm_tc(a, s);
+        if (a.tensor_cores && (a.mode == 0 || a.tensor_cores == 2) && a.chip >= 64 && a.refine == 0)
+            return launch_gamma_gemm_tc(a, s);
     const int tiles = (a.chip + 31) / 32;
     dim3 g2(tiles, tiles, 2 * a.count);
     k_gamma_gemm<R, G><<<g2, 256, 0, s>>>(a);
@@ -786,7 +792,7 @@ template <typename R, typename G> cudaError_t launch_xform(const LayerArgs<R>& a
 }
 template <typename R> cudaError_t launch_proj(const LayerArgs<R>& a, cudaStream_t s) {
     if constexpr (std::is_same<R, float>::value)
-        if (a.tensor_cores && a.chip >= 64 && a.refine == 0) return launch_proj_tc(a, s);
+        if (a.tensor_cores == 2 && a.chip >= 64 && a.refine == 0) return launch_proj_tc(a, s);
     dim3 grid((2 * a.chip + 31) / 32, (a.chip + 31) / 32, a.count);
     k_proj<R><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();

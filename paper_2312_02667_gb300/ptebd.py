@@ -339,7 +339,8 @@ def ptebd_set_svd_polish(h, mode):
 
 
 def ptebd_set_tensor_cores(h, enable):
-    _check(lib.ptebd_set_tensor_cores(h, 1 if enable else 0), h)
+    """enable: False/0 off, True/1 gated stages (default), 2 the tSU steps as well."""
+    _check(lib.ptebd_set_tensor_cores(h, 2 if (enable == 2 and enable is not True) else (1 if enable else 0)), h)
 
 
 def ptebd_set_jacobi_width(h, nw):

@@ -24,12 +24,15 @@ def ptebd():
     return mod
 
 
-@pytest.mark.parametrize("chi,g", [(64, 0), (128, 1)])
-def test_tensor_core_layers_match_cuda_cores_and_oracle(ptebd, chi, g):
+@pytest.mark.parametrize("chi,g,mode", [(64, 0, 1), (128, 1, 1), (128, 1, 2)])
+def test_tensor_core_layers_match_cuda_cores_and_oracle(ptebd, chi, g, mode):
+    # mode 1 (the default): gated stages on the tensor cores; mode 2: the tSU
+    # steps as well
     n, depth = 24, 12
     circuit = inputs.brickwork_circuit(51, n, depth)
     ref = oracle.product_state(n)
     tc = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=g)
+    tc.set_tensor_cores(mode)
     cc = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=g)
     cc.set_tensor_cores(False)
     worst = 0.0
@@ -62,3 +65,32 @@ def test_tensor_core_sampled_bonds_chi256(ptebd):
         oracle.update_bond(mini, 1, env["gate"], chi, 1e-12)
         compare_spectra(got.lambdas[1], mini.lambdas[1], 1e-5, 1e-12, chi)
         ms.close()
+
+
+def test_full_size_ptsu_step_leaves_the_state_as_it_was(ptebd):
+    """A PtSU step does not change the wavefunction (Sec. III D): on the bench's
+    saturated N = 1024, chi = 256 state (gated stages on the tensor cores, the
+    library's default), the state after one more PtSU step has overlap
+    >= 1 - 1e-6 with the state before it and the same norm to 1e-6, both
+    contracted in FP64 (ptebd_overlap / ptebd_norm, pinned to the oracle's
+    contractions elsewhere).  With the tSU steps on the tensor cores as well
+    (ptebd_set_tensor_cores mode 2) the norm moved by 5.4e-4 here: the
+    accumulation's residual shrinkage times the 1023 bonds."""
+    n, chi = 1024, 256
+    st = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=1)
+    for parity, bonds, gates in inputs.brickwork_circuit(7, n, 11):
+        st.apply_layer(gates, parity)
+    assert max(st.chi()) == chi
+    before = ptebd.State(n, chi, "mixed", cutoff=1e-12, g=1)
+    gam, lam = st.export()
+    before.load(gam, lam)
+    del gam, lam
+    n0 = before.norm()
+    st.regauge(1)
+    n1 = st.norm()
+    ov = st.overlap(before)
+    f = abs(complex(ov)) ** 2 / (n0 * n0 * n1 * n1)
+    assert abs(n1 / n0 - 1) <= 1e-6, (n0, n1)
+    assert f >= 1 - 1e-6, f
+    before.close()
+    st.close()
